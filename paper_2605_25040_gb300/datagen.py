@@ -1,0 +1,184 @@
+"""Seeded synthetic key columns shared by the tests and the benchmark.
+
+This module draws random numbers and nothing else: it contains none of the
+sorting method's arithmetic, so both the CUDA path and the CPU oracle can be
+fed from it without sharing any of the method's code.
+
+All randomness comes from SplitMix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) used as a counter-based
+generator: draw i of stream ``seed`` is ``mix(seed + (i + 1) * GAMMA)``.
+
+Workload shapes follow the paper's evaluation (Sec. 6.1): a palette of K
+distinct values, each element picked from it.  The paper's own palette is an
+arithmetic progression ``a + b*i`` with ``a`` and an odd ``b`` derived from
+seed ``42 + N + K`` through a SplitMix-style mixer whose exact form it does not
+give; ``paper_palette`` implements it with SplitMix64, so the paper's datasets
+are reproduced in shape but not bit for bit.  The other generators add what
+the benchmark configurations ask for: values drawn uniformly from the full
+64-bit range, Zipf(s) frequencies, a column whose strided sample positions hold
+a small set while every other element is distinct, and sorted columns.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_MASK64 = (1 << 64) - 1
+
+
+def _u64(x: int) -> np.uint64:
+    return np.uint64(int(x) & _MASK64)
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Draws offset..offset+count-1 of SplitMix64 stream ``seed`` as uint64."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = _u64(seed) + idx * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def _uniform_index(r: np.ndarray, k: int) -> np.ndarray:
+    """Maps uint64 draws to [0, k) by the multiply-high of their top 32 bits."""
+    hi = (r >> np.uint64(32)).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        return ((hi * np.uint64(k)) >> np.uint64(32)).astype(np.int64)
+
+
+def _unit_float(r: np.ndarray) -> np.ndarray:
+    """Maps uint64 draws to doubles in [0, 1) from their top 53 bits."""
+    return (r >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def distinct_values(k: int, seed: int, dtype=np.int64, exclude=None) -> np.ndarray:
+    """K distinct values uniform over the dtype's full range (rejection)."""
+    info = np.iinfo(dtype)
+    out = np.empty(0, dtype=dtype)
+    draw = 0
+    excl = None if exclude is None else np.asarray(exclude, dtype=dtype)
+    while out.size < k:
+        need = k - out.size
+        batch = max(16, int(need * 1.1) + 16)
+        r = splitmix64(seed, batch, offset=draw)
+        draw += batch
+        if dtype == np.int64:
+            v = r.view(np.int64)
+        else:
+            v = (r >> np.uint64(32)).astype(np.uint32).view(np.int32)
+        v = v.astype(dtype, copy=False)
+        cand = np.concatenate([out, v])
+        _, first = np.unique(cand, return_index=True)
+        keep = np.zeros(cand.size, dtype=bool)
+        keep[np.sort(first)] = True
+        if excl is not None and excl.size:
+            keep &= ~np.isin(cand, excl)
+        out = cand[keep][:k]
+        assert out.min() >= info.min and out.max() <= info.max
+    return out
+
+
+def shuffle(values: np.ndarray, seed: int) -> np.ndarray:
+    """Seeded permutation (sort by SplitMix64 draws; ties broken by index)."""
+    r = splitmix64(seed ^ 0x5DEECE66D, values.size)
+    return values[np.argsort(r, kind="stable")]
+
+
+def zipf_ranks(n: int, k: int, s: float, seed: int) -> np.ndarray:
+    """N ranks in [0, K) with P(rank=j) proportional to 1/(j+1)^s.
+
+    Inverse-CDF sampling on the cumulative table of the normalised weights.
+    """
+    w = 1.0 / np.power(np.arange(1, k + 1, dtype=np.float64), s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    u = _unit_float(splitmix64(seed, n))
+    idx = np.searchsorted(cdf, u, side="right")
+    return np.minimum(idx, k - 1).astype(np.int64)
+
+
+def uniform_ranks(n: int, k: int, seed: int) -> np.ndarray:
+    return _uniform_index(splitmix64(seed, n), k)
+
+
+def column(n: int, k: int, dist: str = "uniform", dtype=np.int64, seed: int = 0,
+           s: float = 1.1) -> np.ndarray:
+    """N keys over a palette of K distinct values uniform in the dtype range.
+
+    ``dist`` is "uniform" (every palette value equally likely) or "zipf"
+    (frequency of the j-th most frequent value proportional to 1/j^s; the
+    palette is shuffled so frequency does not follow key order).  When K >= N
+    the column is a permutation of N distinct values (K = N, all distinct).
+    """
+    base = 42 + n + k
+    if k >= n:
+        return shuffle(distinct_values(n, base ^ seed, dtype), base + seed)
+    pal = distinct_values(k, base ^ seed, dtype)
+    pal = shuffle(pal, base + 7 * seed + 1)
+    if dist == "uniform":
+        ranks = uniform_ranks(n, k, base * 31 + seed)
+    elif dist == "zipf":
+        ranks = zipf_ranks(n, k, s, base * 31 + seed)
+    else:
+        raise ValueError(dist)
+    return pal[ranks].astype(dtype, copy=False)
+
+
+def paper_palette(n: int, k: int, dtype=np.int64) -> np.ndarray:
+    """Sec. 6.1 workload: palette a + b*i (b odd), uniform picks, seed 42+N+K."""
+    seed = 42 + n + k
+    r = splitmix64(seed, 2)
+    info = np.iinfo(dtype)
+    bits = 64 if dtype == np.int64 else 32
+    a = int(r[0]) & ((1 << bits) - 1)
+    b = (int(r[1]) & ((1 << bits) - 1)) | 1
+    i = np.arange(k, dtype=object)
+    vals = [((a + b * int(j)) & ((1 << bits) - 1)) for j in i]
+    vals = np.array([v - (1 << bits) if v > info.max else v for v in vals], dtype=dtype)
+    ranks = uniform_ranks(n, k, seed + 1)
+    return vals[ranks]
+
+
+def spill_trigger(n: int, dtype=np.int64, seed: int = 0, small_set: int = 64) -> np.ndarray:
+    """Column whose strided sample positions hold ``small_set`` values only.
+
+    The 1024 sample positions i*stride (stride = max(1, N // 1024)) receive a
+    shuffled multiset of ``small_set`` values, each repeated 1024/small_set
+    times; every other element is a fresh distinct random value not in that
+    set.  A sampler therefore sees a low-cardinality column while the true
+    number of distinct keys is about N.
+    """
+    stride = max(1, n // 1024)
+    npos = min(1024, n)
+    pos = np.arange(npos, dtype=np.int64) * stride
+    small = distinct_values(small_set, 1000 + seed, dtype)
+    reps = -(-npos // small_set)
+    sample_vals = shuffle(np.tile(small, reps)[:npos], 2000 + seed)
+    rest = distinct_values(n - npos, 3000 + seed, dtype, exclude=small)
+    out = np.empty(n, dtype=dtype)
+    mask = np.ones(n, dtype=bool)
+    mask[pos] = False
+    out[pos] = sample_vals
+    out[mask] = rest
+    return out
+
+
+def sorted_column(n: int, k: int, dtype=np.int64, seed: int = 0) -> np.ndarray:
+    return np.sort(column(n, k, "uniform", dtype, seed))
+
+
+def log_uniform_int(lo: float, hi: float, count: int, seed: int) -> np.ndarray:
+    """Integers log-uniform in [lo, hi]."""
+    u = _unit_float(splitmix64(seed, count))
+    return np.floor(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
+
+
+def exponential_gaps(rate: float, count: int, seed: int) -> np.ndarray:
+    """Poisson-process inter-arrival times (seconds) at ``rate`` per second."""
+    u = _unit_float(splitmix64(seed, count))
+    return -np.log1p(-u) / rate
