@@ -1,0 +1,158 @@
+/*
+ * cafs.h -- C ABI of the GB300 (sm_103a) count-and-emit frequency sort.
+ *
+ * The operation is the one the CAFS paper ("CAFS: A Cache-Aware Frequency
+ * Sort for Low-Cardinality Integer Data on x86-64") defines:
+ *
+ *   Sec. 3.1   sort N integer keys ascending; equal keys are
+ *              indistinguishable, so only the values are produced;
+ *   Sec. 4.1   count every distinct key, then emit (key, count) pairs in
+ *              increasing key order;
+ *   Alg. 2     estimate the number of distinct keys K from 1024 strided
+ *              samples with the smoothed Chao1 estimator (Eq. 5);
+ *   Alg. 3     dispatch: already sorted -> bypass, N < 2048 -> direct sort,
+ *              K_hat <= 8 and u <= 8 -> tiny count, 2*K_hat > N -> radix
+ *              fallback, otherwise the hash-count main path;
+ *   Eq. 6      size the hash table M = bit_ceil(8*K_hat/cap), 8 <= M <=
+ *              bit_ceil(N/cap), C = M*cap slots;
+ *   Alg. 4     a guard reroutes to the fallback when the table overflows;
+ *              here the guard fires when the number of distinct keys exceeds
+ *              L = C/2 (an order-independent restatement of the paper's
+ *              insertion-order-dependent spill test).
+ *
+ * Keys are signed two's-complement int32 or int64, sorted ascending.
+ *
+ * Conventions shared by every entry point:
+ *   - Device pointers are caller-owned CUDA device (or managed) memory of n
+ *     elements, naturally aligned for the element type.  `keys` is read-only
+ *     unless out == keys (in-place sorting is allowed); any other overlap of
+ *     the two ranges is rejected with CAFS_ERR_ALIAS.
+ *   - n == 0 is a no-op returning CAFS_OK (NULL pointers allowed then).
+ *   - n must be <= 2^32 - 1 (counts are 32-bit, like the paper's bucket
+ *     counters, Sec. 4.2); larger n returns CAFS_ERR_TOO_LARGE.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) on the current device.  Argument errors are returned
+ *     synchronously and nothing is enqueued.  Device-side failures (a bounded
+ *     wait that ran out) are reported through cafs_report.device_status.
+ *   - The library owns a workspace per (device, stream), allocated on first
+ *     use and grown on demand (growing synchronises the device).  Calls on the
+ *     same stream are serialised by the stream; calls on different streams use
+ *     different workspaces and may overlap.
+ *   - All entry points are thread-safe.
+ */
+#ifndef CAFS_H
+#define CAFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { CAFS_INT32 = 0, CAFS_INT64 = 1 } cafs_dtype;
+
+typedef enum {
+  CAFS_OK = 0,
+  CAFS_ERR_INVALID_ARGUMENT = 1,
+  CAFS_ERR_UNSUPPORTED_DTYPE = 2,
+  CAFS_ERR_TOO_LARGE = 3,
+  CAFS_ERR_ALIAS = 4,
+  CAFS_ERR_OUT_OF_MEMORY = 5,
+  CAFS_ERR_CUDA = 6,
+  CAFS_ERR_TIMEOUT = 7,
+  CAFS_ERR_INTERNAL = 8,
+  CAFS_ERR_BUSY = 9
+} cafs_status;
+
+/* The branch that produced (or, for the dispatcher, was selected for) the
+ * output.  Table 2 / Algorithm 3 give EMPTY..MAIN; the *_RADIX and
+ * TINY_MISS_* values name what happens after the tiny-count check (Sec. 4.4)
+ * and the overflow guard (Alg. 4). */
+typedef enum {
+  CAFS_PATH_EMPTY = 0,
+  CAFS_PATH_BYPASS_SORTED = 1,
+  CAFS_PATH_SMALL_N = 2,
+  CAFS_PATH_TINY = 3,
+  CAFS_PATH_MAIN = 4,
+  CAFS_PATH_HIGH_ENTROPY_RADIX = 5,
+  CAFS_PATH_MAIN_OVERFLOW_RADIX = 6,
+  CAFS_PATH_TINY_MISS_MAIN = 7,
+  CAFS_PATH_TINY_MISS_MAIN_OVERFLOW_RADIX = 8
+} cafs_path;
+
+/* Sampler, Chao1 and sizing results (Alg. 2, Eq. 5, Eq. 6). */
+typedef struct {
+  uint64_t n;          /* number of keys                                    */
+  uint64_t stride;     /* max(1, floor(n / 1024))                           */
+  uint32_t n_samples;  /* min(n, 1024)                                      */
+  uint32_t u;          /* distinct sample values                            */
+  uint32_t f1;         /* sample values seen exactly once                   */
+  uint32_t f2;         /* sample values seen exactly twice                  */
+  uint64_t k_hat;      /* u + floor(f1^2 / (2 (f2 + 1))), or n if u == 1024 */
+  int32_t saturated;   /* 1 when u == 1024                                  */
+  int32_t sample_nondecreasing; /* the samples, in position order, ascend   */
+  uint64_t M;          /* buckets, Eq. 6 with clamps                        */
+  uint64_t C;          /* slots = M * cap (cap 4 for int64, 8 for int32)    */
+  uint64_t L;          /* overflow limit on distinct keys = C / 2           */
+  cafs_path dispatch;  /* Alg. 3 decision: EMPTY, BYPASS_SORTED, SMALL_N,
+                          TINY, HIGH_ENTROPY_RADIX or MAIN                  */
+} cafs_estimate;
+
+/* What a finished sort did. */
+typedef struct {
+  cafs_estimate est;   /* the estimate the dispatcher used               */
+  cafs_path path;      /* branch that produced the output                */
+  uint64_t k_distinct; /* distinct keys counted (TINY, MAIN, TINY_MISS_MAIN
+                          paths); 0 when the branch does not count        */
+  cafs_status device_status; /* CAFS_OK or CAFS_ERR_TIMEOUT               */
+} cafs_report;
+
+/* Sort n keys from `keys` into `out` (ascending, signed), asynchronously on
+ * `stream`.  Implements Sec. 3.1 via Algorithms 2-4.  Returns after
+ * enqueueing.  `keys` and `out` are device pointers (see conventions). */
+cafs_status cafs_sort(const void* keys, size_t n, cafs_dtype dtype, void* out,
+                      void* stream);
+
+/* As cafs_sort; when `report` (host memory) is non-NULL the call waits for
+ * the stream and fills *report with the estimate, the branch taken, the
+ * number of distinct keys counted and the device status.  With report == NULL
+ * it behaves exactly like cafs_sort. */
+cafs_status cafs_sort_ex(const void* keys, size_t n, cafs_dtype dtype, void* out,
+                         cafs_report* report, void* stream);
+
+/* Sampler + Chao1 + dispatcher only (Alg. 2 and Alg. 3, Eq. 5-6): fills *est
+ * (host memory).  Blocking: waits for `stream`.  The IsMonotone test of
+ * Alg. 3 is a full scan on the device, run only when the samples ascend. */
+cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype,
+                            cafs_estimate* est, void* stream);
+
+/* End-to-end form for host buffers: copies n keys from host memory
+ * `host_keys` to a library-owned device buffer, sorts them on the device and
+ * copies the result to host memory `host_out` (which may equal host_keys).
+ * Blocking.  Pinned host memory gives the fastest copies; pageable memory
+ * works.  `report` may be NULL. */
+cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype,
+                           void* host_out, cafs_report* report, void* stream);
+
+/* Testing hooks (no counterpart in the paper).  `flags` bit 0 makes CTA 0 of
+ * the next pipeline launches skip the first grid barrier, so that the other
+ * CTAs' bounded wait runs out and the launch reports CAFS_ERR_TIMEOUT in
+ * cafs_report.device_status; no GPU fault is involved.  `wait_timeout_ns`
+ * bounds every device-side wait (0 restores the default of one second).
+ * Pass flags = 0 to return to normal operation. */
+void cafs_set_test_hooks(uint32_t flags, uint64_t wait_timeout_ns);
+
+/* Number of kernels the library launched on the calling process so far
+ * (all entry points, all devices).  Diagnostic counter. */
+uint64_t cafs_kernel_launch_count(void);
+
+/* Human-readable names; never NULL. */
+const char* cafs_status_string(cafs_status s);
+const char* cafs_path_string(cafs_path p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CAFS_H */

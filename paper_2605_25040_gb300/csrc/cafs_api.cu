@@ -1,0 +1,415 @@
+// Host runtime and C ABI (include/cafs.h): argument checks, per-(device,
+// stream) workspaces, launch of the pipeline kernels, report read-back.
+
+#include <atomic>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "cafs.h"
+#include "cafs_internal.h"
+
+namespace cafs {
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_mu;
+unsigned g_test_flags = 0;
+unsigned long long g_timeout_ns = 1000000000ull;  // bounded device waits: 1 s
+
+struct DeviceInfo {
+  bool ready = false;
+  int sms = 0;
+  int max_grid[2] = {0, 0};
+};
+std::map<int, DeviceInfo> g_dev;
+
+struct Workspace {
+  int device = -1;
+  unsigned gen = 0;
+  // capacities
+  unsigned long long n_cap = 0;        // keys the radix temp holds (per dtype bytes)
+  size_t tmp_bytes = 0;
+  unsigned long long table_cap = 0;
+  unsigned long long pair_cap = 0;
+  unsigned long long lookback_cap = 0;
+  size_t io_bytes = 0;
+  // device buffers
+  Ctrl* ctrl = nullptr;
+  unsigned long long* tkeys = nullptr;
+  unsigned* tcounts = nullptr;
+  unsigned* claimed = nullptr;
+  void* pkeys_a = nullptr; unsigned* pvals_a = nullptr;
+  void* pkeys_b = nullptr; unsigned* pvals_b = nullptr;
+  void* skeys = nullptr; unsigned* svals = nullptr;
+  unsigned* offsets = nullptr;
+  void* tmp = nullptr;
+  unsigned long long* lookback = nullptr;
+  void* io = nullptr;
+  Record* host_rec = nullptr;  // pinned
+};
+std::map<std::pair<int, uintptr_t>, Workspace*> g_ws;
+
+unsigned long long bit_ceil_host(unsigned long long x) {
+  unsigned long long r = 1;
+  while (r < x) r <<= 1;
+  return r;
+}
+
+// Largest Chao1 estimate short of saturation: u = 1022 distinct samples, 1021
+// of them seen once and one seen three times (Eq. 5 maximised over the sample
+// spectra with u < 1024).  Any main-path table is sized from K_hat <= this.
+constexpr unsigned long long kMaxUnsaturatedKhat = 522242ull;
+
+unsigned long long table_capacity(unsigned long long n, int dtype) {
+  const unsigned long long cap = dtype == CAFS_INT64 ? 4 : 8;
+  unsigned long long m = bit_ceil_host((8ull * kMaxUnsaturatedKhat) / cap);
+  const unsigned long long upper = bit_ceil_host((n + cap - 1) / cap);
+  if (m > upper) m = upper;
+  if (m < 8) m = 8;
+  return m * cap;
+}
+
+template <typename T>
+void free_dev(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+void release_buffers(Workspace* w) {
+  free_dev(w->ctrl); free_dev(w->tkeys); free_dev(w->tcounts); free_dev(w->claimed);
+  free_dev(w->pkeys_a); free_dev(w->pvals_a); free_dev(w->pkeys_b); free_dev(w->pvals_b);
+  free_dev(w->skeys); free_dev(w->svals); free_dev(w->offsets); free_dev(w->tmp);
+  free_dev(w->lookback);
+  w->n_cap = 0; w->tmp_bytes = 0; w->table_cap = 0; w->pair_cap = 0; w->lookback_cap = 0;
+}
+
+cafs_status ensure_device(int dev, DeviceInfo** out) {
+  DeviceInfo& d = g_dev[dev];
+  if (!d.ready) {
+    if (prepare_kernels() != cudaSuccess) return CAFS_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CAFS_ERR_CUDA;
+    for (int t = 0; t < 2; ++t) {
+      int bps = 0;
+      if (pipeline_occupancy(t, &bps) != cudaSuccess || bps < 1) return CAFS_ERR_CUDA;
+      long long g = (long long)bps * d.sms;
+      if (g > 1024) g = 1024;  // Ctrl::chunk_sums holds one partial sum per CTA
+      d.max_grid[t] = (int)g;
+    }
+    d.ready = true;
+  }
+  *out = &d;
+  return CAFS_OK;
+}
+
+template <typename T>
+cudaError_t alloc(T** p, size_t bytes) {
+  return cudaMalloc((void**)p, bytes < 16 ? 16 : bytes);
+}
+
+// Makes the workspace big enough for n keys of dtype; call with g_mu held.
+cafs_status ensure_workspace(Workspace* w, unsigned long long n, int dtype, cudaStream_t s,
+                             bool need_io) {
+  const size_t kb = dtype == CAFS_INT64 ? 8 : 4;
+  const unsigned long long tcap = table_capacity(n, dtype);
+  unsigned long long pcap = tcap / 2 + 2;
+  if (pcap < (unsigned long long)kSmallPairs) pcap = kSmallPairs;
+  const unsigned long long items = n > pcap ? n : pcap;
+  const unsigned long long lcap = ((items + kRadixTile - 1) / kRadixTile) * kRadixDigits;
+  const size_t tmp_bytes = (size_t)n * kb;
+  const bool grow = !w->ctrl || tcap > w->table_cap || pcap > w->pair_cap ||
+                    lcap > w->lookback_cap || tmp_bytes > w->tmp_bytes;
+  if (grow) {
+    if (w->ctrl && cudaStreamSynchronize(s) != cudaSuccess) return CAFS_ERR_CUDA;
+    const unsigned long long ntc = tcap > w->table_cap ? tcap : w->table_cap;
+    const unsigned long long npc = pcap > w->pair_cap ? pcap : w->pair_cap;
+    const unsigned long long nlc = lcap > w->lookback_cap ? lcap : w->lookback_cap;
+    const size_t ntb = tmp_bytes > w->tmp_bytes ? tmp_bytes : w->tmp_bytes;
+    release_buffers(w);
+    bool ok = alloc(&w->ctrl, sizeof(Ctrl)) == cudaSuccess &&
+              alloc(&w->tkeys, ntc * 8) == cudaSuccess &&
+              alloc(&w->tcounts, ntc * 4) == cudaSuccess &&
+              alloc(&w->claimed, ntc * 4) == cudaSuccess &&
+              alloc(&w->pkeys_a, npc * 8) == cudaSuccess &&
+              alloc(&w->pvals_a, npc * 4) == cudaSuccess &&
+              alloc(&w->pkeys_b, npc * 8) == cudaSuccess &&
+              alloc(&w->pvals_b, npc * 4) == cudaSuccess &&
+              alloc(&w->skeys, npc * 8) == cudaSuccess &&
+              alloc(&w->svals, npc * 4) == cudaSuccess &&
+              alloc(&w->offsets, (npc + 2) * 4) == cudaSuccess &&
+              alloc(&w->tmp, ntb) == cudaSuccess &&
+              alloc(&w->lookback, nlc * 8) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      release_buffers(w);
+      return CAFS_ERR_OUT_OF_MEMORY;
+    }
+    // Empty table: every key slot holds the empty marker, every count 0.
+    if (launch_fill_u64(w->tkeys, ntc, 0x8000000000000000ull, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    g_launches++;
+    if (cudaMemsetAsync(w->tcounts, 0, ntc * 4, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    if (cudaMemsetAsync(w->lookback, 0, nlc * 8, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    w->table_cap = ntc; w->pair_cap = npc; w->lookback_cap = nlc; w->tmp_bytes = ntb;
+    w->n_cap = n;
+  }
+  if (!w->host_rec) {
+    if (cudaMallocHost((void**)&w->host_rec, sizeof(Record)) != cudaSuccess) return CAFS_ERR_OUT_OF_MEMORY;
+  }
+  if (need_io && (size_t)n * kb > w->io_bytes) {
+    if (w->io) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return CAFS_ERR_CUDA;
+      cudaFree(w->io);
+      w->io = nullptr;
+    }
+    if (alloc(&w->io, (size_t)n * kb) != cudaSuccess) {
+      cudaGetLastError();
+      w->io_bytes = 0;
+      return CAFS_ERR_OUT_OF_MEMORY;
+    }
+    w->io_bytes = (size_t)n * kb;
+  }
+  return CAFS_OK;
+}
+
+Workspace* workspace_for(int dev, cudaStream_t s) {
+  auto key = std::make_pair(dev, reinterpret_cast<uintptr_t>(s));
+  auto it = g_ws.find(key);
+  if (it != g_ws.end()) return it->second;
+  Workspace* w = new Workspace();
+  w->device = dev;
+  g_ws[key] = w;
+  return w;
+}
+
+cafs_status check_args(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out) {
+  if (dtype != CAFS_INT32 && dtype != CAFS_INT64) return CAFS_ERR_UNSUPPORTED_DTYPE;
+  if (n == 0) return CAFS_OK;
+  if ((unsigned long long)n > 0xFFFFFFFFull) return CAFS_ERR_TOO_LARGE;
+  const size_t kb = dtype == CAFS_INT64 ? 8 : 4;
+  if (!keys || (need_out && !out)) return CAFS_ERR_INVALID_ARGUMENT;
+  if (reinterpret_cast<uintptr_t>(keys) % kb) return CAFS_ERR_INVALID_ARGUMENT;
+  if (need_out) {
+    if (reinterpret_cast<uintptr_t>(out) % kb) return CAFS_ERR_INVALID_ARGUMENT;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(keys), b0 = reinterpret_cast<uintptr_t>(out);
+    const uintptr_t bytes = (uintptr_t)n * kb;
+    if (a0 != b0 && a0 < b0 + bytes && b0 < a0 + bytes) return CAFS_ERR_ALIAS;
+  }
+  return CAFS_OK;
+}
+
+void fill_estimate(const Record& r, cafs_estimate* e) {
+  e->n = r.n;
+  e->stride = r.stride;
+  e->n_samples = r.n_samples;
+  e->u = r.u;
+  e->f1 = r.f1;
+  e->f2 = r.f2;
+  e->k_hat = r.k_hat;
+  e->saturated = r.saturated;
+  e->sample_nondecreasing = r.sample_nondecreasing;
+  e->M = r.M;
+  e->C = r.C;
+  e->L = r.L;
+  e->dispatch = (cafs_path)r.dispatch;
+}
+
+// Enqueues one pipeline run on stream s (g_mu held).
+cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* out,
+                    unsigned long long n, int dtype, int mode, cudaStream_t s) {
+  if (cudaMemsetAsync(w->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+  Params p;
+  std::memset(&p, 0, sizeof(p));
+  p.keys = keys;
+  p.out = out;
+  p.n = n;
+  p.ctrl = w->ctrl;
+  p.tkeys = w->tkeys;
+  p.tcounts = w->tcounts;
+  p.claimed = w->claimed;
+  p.table_cap = w->table_cap;
+  p.pkeys_a = w->pkeys_a; p.pvals_a = w->pvals_a;
+  p.pkeys_b = w->pkeys_b; p.pvals_b = w->pvals_b;
+  p.skeys = w->skeys; p.svals = w->svals;
+  p.offsets = w->offsets;
+  p.pair_cap = w->pair_cap;
+  p.tmp = w->tmp;
+  p.lookback = w->lookback;
+  p.lookback_cap = w->lookback_cap;
+  p.gen = ++w->gen;
+  p.mode = mode;
+  p.test_flags = g_test_flags;
+  p.timeout_ns = g_timeout_ns;
+  cudaError_t e;
+  if (n < kSmallN) {
+    e = launch_small(p, dtype, s);
+  } else {
+    long long grid = (long long)((n + 16383) / 16384);
+    if (grid > d->max_grid[dtype]) grid = d->max_grid[dtype];
+    if (grid < 1) grid = 1;
+    e = launch_pipeline(p, dtype, (int)grid, s);
+  }
+  if (e != cudaSuccess) return CAFS_ERR_CUDA;
+  g_launches++;
+  return CAFS_OK;
+}
+
+cafs_status read_record(Workspace* w, cudaStream_t s, Record* r) {
+  if (cudaMemcpyAsync(w->host_rec, &w->ctrl->rec, sizeof(Record), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CAFS_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CAFS_ERR_CUDA;
+  *r = *w->host_rec;
+  return CAFS_OK;
+}
+
+void fill_report(const Record& r, cafs_report* rep) {
+  std::memset(rep, 0, sizeof(*rep));
+  fill_estimate(r, &rep->est);
+  rep->path = (cafs_path)r.path;
+  rep->k_distinct = r.k_distinct;
+  rep->device_status = (cafs_status)r.status;
+}
+
+cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, cafs_report* report,
+                      void* stream) {
+  cafs_status st = check_args(keys, n, dtype, out, true);
+  if (st != CAFS_OK) return st;
+  if (n == 0) {
+    if (report) {
+      std::memset(report, 0, sizeof(*report));
+      report->path = CAFS_PATH_EMPTY;
+      report->est.dispatch = CAFS_PATH_EMPTY;
+    }
+    return CAFS_OK;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CAFS_ERR_CUDA;
+  DeviceInfo* d = nullptr;
+  if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
+  Workspace* w = workspace_for(dev, s);
+  if ((st = ensure_workspace(w, n, dtype, s, false)) != CAFS_OK) return st;
+  if ((st = enqueue(w, d, keys, out, n, dtype, kModeSort, s)) != CAFS_OK) return st;
+  if (report) {
+    Record r;
+    if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
+    fill_report(r, report);
+  }
+  return CAFS_OK;
+}
+
+}  // namespace
+}  // namespace cafs
+
+using namespace cafs;
+
+extern "C" {
+
+cafs_status cafs_sort(const void* keys, size_t n, cafs_dtype dtype, void* out, void* stream) {
+  return sort_impl(keys, n, dtype, out, nullptr, stream);
+}
+
+cafs_status cafs_sort_ex(const void* keys, size_t n, cafs_dtype dtype, void* out,
+                         cafs_report* report, void* stream) {
+  return sort_impl(keys, n, dtype, out, report, stream);
+}
+
+cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype, cafs_estimate* est,
+                            void* stream) {
+  if (!est) return CAFS_ERR_INVALID_ARGUMENT;
+  cafs_status st = check_args(keys, n, dtype, nullptr, false);
+  if (st != CAFS_OK) return st;
+  std::memset(est, 0, sizeof(*est));
+  if (n == 0) {
+    est->dispatch = CAFS_PATH_EMPTY;
+    return CAFS_OK;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CAFS_ERR_CUDA;
+  DeviceInfo* d = nullptr;
+  if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
+  Workspace* w = workspace_for(dev, s);
+  if ((st = ensure_workspace(w, n, dtype, s, false)) != CAFS_OK) return st;
+  if ((st = enqueue(w, d, keys, nullptr, n, dtype, kModeEstimate, s)) != CAFS_OK) return st;
+  Record r;
+  if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
+  if (r.status != kDevOk) return (cafs_status)r.status;
+  fill_estimate(r, est);
+  return CAFS_OK;
+}
+
+cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype, void* host_out,
+                           cafs_report* report, void* stream) {
+  cafs_status st = check_args(host_keys, n, dtype, host_out, false);
+  if (st != CAFS_OK) return st;
+  if (n && !host_out) return CAFS_ERR_INVALID_ARGUMENT;
+  if (n == 0) {
+    if (report) {
+      std::memset(report, 0, sizeof(*report));
+      report->path = CAFS_PATH_EMPTY;
+    }
+    return CAFS_OK;
+  }
+  const size_t bytes = n * (dtype == CAFS_INT64 ? 8 : 4);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CAFS_ERR_CUDA;
+  DeviceInfo* d = nullptr;
+  if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
+  Workspace* w = workspace_for(dev, s);
+  if ((st = ensure_workspace(w, n, dtype, s, true)) != CAFS_OK) return st;
+  if (cudaMemcpyAsync(w->io, host_keys, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return CAFS_ERR_CUDA;
+  if ((st = enqueue(w, d, w->io, w->io, n, dtype, kModeSort, s)) != CAFS_OK) return st;
+  if (cudaMemcpyAsync(host_out, w->io, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CAFS_ERR_CUDA;
+  Record r;
+  if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
+  if (report) fill_report(r, report);
+  return CAFS_OK;
+}
+
+void cafs_set_test_hooks(uint32_t flags, uint64_t wait_timeout_ns) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_test_flags = flags;
+  g_timeout_ns = wait_timeout_ns ? wait_timeout_ns : 1000000000ull;
+}
+
+uint64_t cafs_kernel_launch_count(void) { return g_launches.load(); }
+
+const char* cafs_status_string(cafs_status s) {
+  switch (s) {
+    case CAFS_OK: return "ok";
+    case CAFS_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case CAFS_ERR_UNSUPPORTED_DTYPE: return "unsupported dtype";
+    case CAFS_ERR_TOO_LARGE: return "n exceeds 2^32-1";
+    case CAFS_ERR_ALIAS: return "keys and out overlap partially";
+    case CAFS_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case CAFS_ERR_CUDA: return "CUDA runtime error";
+    case CAFS_ERR_TIMEOUT: return "bounded device wait timed out";
+    case CAFS_ERR_INTERNAL: return "internal error";
+    case CAFS_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+const char* cafs_path_string(cafs_path p) {
+  switch (p) {
+    case CAFS_PATH_EMPTY: return "empty";
+    case CAFS_PATH_BYPASS_SORTED: return "bypass_sorted";
+    case CAFS_PATH_SMALL_N: return "small_n";
+    case CAFS_PATH_TINY: return "tiny";
+    case CAFS_PATH_MAIN: return "main";
+    case CAFS_PATH_HIGH_ENTROPY_RADIX: return "high_entropy_radix";
+    case CAFS_PATH_MAIN_OVERFLOW_RADIX: return "main_overflow_radix";
+    case CAFS_PATH_TINY_MISS_MAIN: return "tiny_miss_main";
+    case CAFS_PATH_TINY_MISS_MAIN_OVERFLOW_RADIX: return "tiny_miss_main_overflow_radix";
+  }
+  return "unknown path";
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Internal definitions shared by the kernels (cafs_pipeline.cu) and the host
+// runtime (cafs_api.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace cafs {
+
+// Algorithm 2: number of strided samples s.
+constexpr int kSamples = 1024;
+// Table 2 / Algorithm 3: below this length the sampler is skipped.
+constexpr uint64_t kSmallN = 2048;
+// Table 2: tiny-count branch limit on K_hat and u.
+constexpr int kTinyMax = 8;
+
+// Threads per CTA of every kernel in the library.
+constexpr int kThreads = 1024;
+constexpr int kWarps = kThreads / 32;
+
+// Dynamic shared memory of the persistent pipeline kernel (bytes).  The
+// per-CTA hash table of the count phase is the largest tenant.
+constexpr int kPipelineSmem = 200 * 1024;
+// Largest per-CTA shared hash table (slots); 12 B per slot for int64 keys.
+constexpr int kLocalSlotsMax = 16384;
+// Pair counts up to this size are sorted by one CTA in shared memory.
+constexpr int kSmallPairs = 8192;
+// Radix sort: 8-bit digits; items per thread per tile.
+constexpr int kRadixBits = 8;
+constexpr int kRadixDigits = 1 << kRadixBits;
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kThreads * kRadixItems;
+// Emit: elements per output tile and pairs staged per tile in shared memory.
+constexpr int kEmitStagePairs = 4096;
+
+// Device status codes (match cafs_status values).
+constexpr unsigned kDevOk = 0;
+constexpr unsigned kDevTimeout = 7;
+constexpr unsigned kDevInternal = 8;
+
+// Pipeline modes.
+constexpr int kModeSort = 0;
+constexpr int kModeEstimate = 1;
+
+// Test hooks (bit flags in Params::test_flags).
+constexpr unsigned kTestSkipBarrier = 1u;   // CTA 0 never arrives: the others time out
+
+// Result of the sampler / dispatcher, written by the device.
+struct Record {
+  unsigned long long n, stride, k_hat, M, C, L;
+  unsigned n_samples, u, f1, f2;
+  int saturated, sample_nondecreasing;
+  int dispatch;   // Algorithm 3 decision
+  int path;       // final branch
+  int n_tiny;
+  int pad0;
+  long long tiny_keys[kTinyMax];  // the u <= 8 distinct sample values, ascending
+  unsigned long long k_distinct;  // distinct keys counted (K')
+  unsigned long long n_pairs;     // entries in the sorted pair arrays (padded)
+  unsigned status;                // kDevOk / kDevTimeout / ...
+  unsigned pad1;
+};
+
+// Control block: zeroed by the host before every pipeline launch.
+struct Ctrl {
+  Record rec;
+  unsigned bar_count;
+  unsigned bar_epoch;
+  unsigned occupancy;           // global-table slots claimed
+  unsigned overflow;            // guard fired (distinct keys > L or table full)
+  unsigned inversion;           // IsMonotone found a descent
+  unsigned pad2;
+  unsigned long long special;   // keys equal to the type minimum (the empty marker)
+  unsigned long long miss;      // tiny path: keys outside the sampled set
+  unsigned tickets[16];         // radix: per-pass tile tickets
+  unsigned hist[8][kRadixDigits];  // radix: global digit counts per pass
+  unsigned long long chunk_sums[1024];  // scan: per-CTA partial sums
+};
+
+struct Params {
+  const void* keys;
+  void* out;
+  unsigned long long n;
+  Ctrl* ctrl;
+  // global hash table (C slots used, capacity table_cap)
+  unsigned long long* tkeys;
+  unsigned* tcounts;
+  unsigned* claimed;
+  unsigned long long table_cap;
+  // pair arrays: A (gathered), B (radix temp), S (sorted) + offsets
+  void* pkeys_a; unsigned* pvals_a;
+  void* pkeys_b; unsigned* pvals_b;
+  void* skeys;   unsigned* svals;
+  unsigned* offsets;
+  unsigned long long pair_cap;
+  // radix fallback temp buffer (n keys) and look-back status words
+  void* tmp;
+  unsigned long long* lookback;
+  unsigned long long lookback_cap;   // words
+  unsigned gen;          // call generation (tags look-back words)
+  int mode;
+  unsigned test_flags;
+  unsigned long long timeout_ns;
+};
+
+// Host-side launchers (defined in cafs_pipeline.cu).
+cudaError_t launch_pipeline(const Params& p, int dtype, int grid, cudaStream_t s);
+cudaError_t launch_small(const Params& p, int dtype, cudaStream_t s);
+cudaError_t pipeline_occupancy(int dtype, int* blocks_per_sm);
+cudaError_t prepare_kernels();
+cudaError_t launch_fill_u64(unsigned long long* ptr, unsigned long long n, unsigned long long v,
+                            cudaStream_t s);
+
+}  // namespace cafs

@@ -1,0 +1,69 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every function include/cafs.h declares, and rejects bad arguments before any
+device work (these paths never touch CUDA)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_25040_gb300 import build as B
+from paper_2605_25040_gb300 import cafs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(cafs_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return cafs.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert "cafs_sort" in declared and "cafs_estimate_k" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) <= set(cafs.SIGNATURES), "binding misses a declared function"
+
+
+def test_argument_errors_are_synchronous(lib):
+    buf = (ctypes.c_int64 * 16)()
+    p = ctypes.addressof(buf)
+    # unsupported dtype
+    assert lib.cafs_sort(p, 4, 7, p + 64, None) == 2
+    # n == 0 is a no-op even with NULL pointers
+    assert lib.cafs_sort(None, 0, cafs.INT64, None, None) == 0
+    # n > 2^32 - 1
+    assert lib.cafs_sort(p, 1 << 32, cafs.INT64, p + 64, None) == 3
+    # NULL keys / out
+    assert lib.cafs_sort(None, 4, cafs.INT64, p, None) == 1
+    assert lib.cafs_sort(p, 4, cafs.INT64, None, None) == 1
+    # misaligned for the element type
+    assert lib.cafs_sort(p + 4, 4, cafs.INT64, p + 64, None) == 1
+    # partial overlap of keys and out
+    assert lib.cafs_sort(p, 8, cafs.INT64, p + 8, None) == 4
+    est = cafs.Estimate()
+    assert lib.cafs_estimate_k(p, 4, 9, ctypes.byref(est), None) == 2
+    assert lib.cafs_estimate_k(p, 4, cafs.INT64, None, None) == 1
+
+
+def test_names(lib):
+    assert lib.cafs_status_string(0) == b"ok"
+    assert lib.cafs_path_string(4) == b"main"
+    assert lib.cafs_path_string(8) == b"tiny_miss_main_overflow_radix"
+    for code, name in cafs.PATHS.items():
+        assert lib.cafs_path_string(code).decode() == name
