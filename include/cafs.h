@@ -106,6 +106,11 @@ typedef struct {
   uint64_t k_distinct; /* distinct keys counted (TINY, MAIN, TINY_MISS_MAIN
                           paths); 0 when the branch does not count        */
   cafs_status device_status; /* CAFS_OK or CAFS_ERR_TIMEOUT               */
+  /* Device timestamps (ns, GPU global timer) at the pipeline's phase
+   * boundaries: [0] start, [1] sampled, [2] monotone scan done, [3] counted,
+   * [4] pairs sorted and scanned, [5] last CTA finished; 0 where a phase did
+   * not run (N < 2048 columns report none). */
+  uint64_t timeline_ns[6];
 } cafs_report;
 
 /* Sort n keys from `keys` into `out` (ascending, signed), asynchronously on

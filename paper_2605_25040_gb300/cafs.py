@@ -44,11 +44,11 @@ class Estimate(ctypes.Structure):
 
 class Report(ctypes.Structure):
     _fields_ = [("est", Estimate), ("path", ctypes.c_int), ("k_distinct", ctypes.c_uint64),
-                ("device_status", ctypes.c_int)]
+                ("device_status", ctypes.c_int), ("timeline_ns", ctypes.c_uint64 * 6)]
 
     def as_dict(self) -> dict:
         return {"est": self.est.as_dict(), "path": self.path, "k_distinct": self.k_distinct,
-                "device_status": self.device_status}
+                "device_status": self.device_status, "timeline_ns": list(self.timeline_ns)}
 
 
 class CafsError(RuntimeError):

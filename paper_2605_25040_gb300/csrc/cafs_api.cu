@@ -48,6 +48,7 @@ struct Workspace {
   unsigned* offsets = nullptr;
   void* tmp = nullptr;
   unsigned long long* lookback = nullptr;
+  long long* sample_keys = nullptr;
   void* io = nullptr;
   Record* host_rec = nullptr;  // pinned
 };
@@ -83,7 +84,7 @@ void release_buffers(Workspace* w) {
   free_dev(w->ctrl); free_dev(w->tkeys); free_dev(w->tcounts); free_dev(w->claimed);
   free_dev(w->pkeys_a); free_dev(w->pvals_a); free_dev(w->pkeys_b); free_dev(w->pvals_b);
   free_dev(w->skeys); free_dev(w->svals); free_dev(w->offsets); free_dev(w->tmp);
-  free_dev(w->lookback);
+  free_dev(w->lookback); free_dev(w->sample_keys);
   w->n_cap = 0; w->tmp_bytes = 0; w->table_cap = 0; w->pair_cap = 0; w->lookback_cap = 0;
 }
 
@@ -141,7 +142,8 @@ cafs_status ensure_workspace(Workspace* w, unsigned long long n, int dtype, cuda
               alloc(&w->svals, npc * 4) == cudaSuccess &&
               alloc(&w->offsets, (npc + 2) * 4) == cudaSuccess &&
               alloc(&w->tmp, ntb) == cudaSuccess &&
-              alloc(&w->lookback, nlc * 8) == cudaSuccess;
+              alloc(&w->lookback, nlc * 8) == cudaSuccess &&
+              alloc(&w->sample_keys, kSamples * 8) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       release_buffers(w);
@@ -238,6 +240,7 @@ cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* o
   p.tmp = w->tmp;
   p.lookback = w->lookback;
   p.lookback_cap = w->lookback_cap;
+  p.sample_keys = w->sample_keys;
   p.gen = ++w->gen;
   p.mode = mode;
   p.test_flags = g_test_flags;
@@ -270,6 +273,7 @@ void fill_report(const Record& r, cafs_report* rep) {
   rep->path = (cafs_path)r.path;
   rep->k_distinct = r.k_distinct;
   rep->device_status = (cafs_status)r.status;
+  for (int i = 0; i < 6; ++i) rep->timeline_ns[i] = r.timeline[i];
 }
 
 cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, cafs_report* report,

@@ -14,17 +14,46 @@ constexpr int kSamples = 1024;
 constexpr uint64_t kSmallN = 2048;
 // Table 2: tiny-count branch limit on K_hat and u.
 constexpr int kTinyMax = 8;
+// Tiny path: the sampled keys are hashed collision-free into this many
+// buckets (log2: kTinyBucketBits) by a multiplier found during sampling.
+constexpr int kTinyBucketBits = 4;
+constexpr int kTinyBuckets = 1 << kTinyBucketBits;
 
-// Threads per CTA of every kernel in the library.
+// Threads per CTA of every kernel in the library (one CTA per SM).
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 
-// Dynamic shared memory of the persistent pipeline kernel (bytes).  The
-// per-CTA hash table of the count phase is the largest tenant.
-constexpr int kPipelineSmem = 200 * 1024;
-// Largest per-CTA shared hash table (slots); 12 B per slot for int64 keys.
-constexpr int kLocalSlotsMax = 16384;
-// Pair counts up to this size are sorted by one CTA in shared memory.
+// Dynamic shared memory of the persistent pipeline kernel (bytes): during
+// the count phase it holds the bulk-copy ring and the per-CTA hash table.
+constexpr int kPipelineSmem = 226 * 1024;
+// Count phase: one producer warp streams the CTA's share of the column
+// through a ring of chunks with cp.async.bulk; the other warps
+// consume.  A chunk is kVecsPerThread 16-byte vectors per consumer thread.
+constexpr int kConsumerWarps = kWarps - 1;
+constexpr int kVecsPerThread = 2;
+constexpr int kChunkVecs = kConsumerWarps * 32 * kVecsPerThread;
+constexpr int kChunkBytes = kChunkVecs * 16;
+// The ring sits at the top of shared memory (about 128 KB must be in flight
+// per SM to reach full read bandwidth); it is filled from the start of the
+// launch, while CTA 0 samples, and never overlaps the sampler's or the count
+// phase's tables below it.
+constexpr int kRingStages = 4;
+constexpr int kRingBytes = kRingStages * kChunkBytes;
+// Shared-memory budget of the per-CTA hash table (keys + counters), of the
+// small bookkeeping area before it, and of the tiny path's table (the tiny
+// path's per-thread bucket counters follow it inside the table budget).
+constexpr int kLocalTableBytes = 96 * 1024;
+constexpr int kSmallTableBytes = 48 * 1024;   // R is trimmed to this for S <= 2048
+constexpr int kMiscBytes = 512;
+constexpr int kTinyTableBytes = 36 * 1024;
+// Largest per-CTA shared hash table (slots).
+constexpr int kLocalSlotsMax = 8192;
+// Pair counts up to this size are ordered by an all-CTA rank computation;
+// larger counts go through the LSD radix sort.
+constexpr int kRankPairs = 4096;
+// Columns shorter than this are sorted by one CTA in shared memory.
+constexpr int kSmallCap = 2048;
+// Pair arrays hold at least this many entries.
 constexpr int kSmallPairs = 8192;
 // Radix sort: 8-bit digits; items per thread per tile.
 constexpr int kRadixBits = 8;
@@ -56,10 +85,14 @@ struct Record {
   int n_tiny;
   int pad0;
   long long tiny_keys[kTinyMax];  // the u <= 8 distinct sample values, ascending
+  unsigned long long tiny_mult;   // odd multiplier hashing the tiny keys to distinct
+  int tiny_hash_ok;               //   buckets of kTinyBuckets (0: none found)
+  int pad_t;
   unsigned long long k_distinct;  // distinct keys counted (K')
   unsigned long long n_pairs;     // entries in the sorted pair arrays (padded)
   unsigned status;                // kDevOk / kDevTimeout / ...
   unsigned pad1;
+  unsigned long long timeline[8]; // globaltimer ns at phase boundaries
 };
 
 // Control block: zeroed by the host before every pipeline launch.
@@ -72,7 +105,7 @@ struct Ctrl {
   unsigned inversion;           // IsMonotone found a descent
   unsigned pad2;
   unsigned long long special;   // keys equal to the type minimum (the empty marker)
-  unsigned long long miss;      // tiny path: keys outside the sampled set
+  unsigned long long unused0;
   unsigned tickets[16];         // radix: per-pass tile tickets
   unsigned hist[8][kRadixDigits];  // radix: global digit counts per pass
   unsigned long long chunk_sums[1024];  // scan: per-CTA partial sums
@@ -98,6 +131,7 @@ struct Params {
   void* tmp;
   unsigned long long* lookback;
   unsigned long long lookback_cap;   // words
+  long long* sample_keys;            // kSamples: distinct sampled keys, ascending
   unsigned gen;          // call generation (tags look-back words)
   int mode;
   unsigned test_flags;

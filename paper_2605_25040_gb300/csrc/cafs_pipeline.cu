@@ -7,14 +7,18 @@
 //                                                    Alg. 3; CTA 0)
 //   1  IsMonotone full scan, only when the 1024 samples ascend (Alg. 3);
 //      a sorted column is copied through (bypass)
-//   2  count: tiny path (K_hat <= 8, u <= 8: register counters per thread,
-//      Sec. 4.4) or main path (per-CTA shared-memory open-addressing table,
-//      merged into a global table hashed with Eq. 4, Sec. 4.2); the global
-//      table counts distinct keys and raises the overflow guard when they
-//      exceed L = C/2 (Eq. 6, Alg. 4)
-//   3  the K' (key, count) pairs are sorted by key (Alg. 4): one CTA in shared
-//      memory when K' <= 8192, otherwise an LSD radix sort over all CTAs;
-//      then an exclusive scan of the counts gives each run's output offset
+//   2  count: every CTA streams its share of the column through a shared
+//      memory ring filled by bulk copies (cp.async.bulk + mbarrier) and counts
+//      it, either against the <= 8 sampled keys in registers (tiny path,
+//      Sec. 4.4) or in a per-CTA open-addressing table (main path, Sec. 4.2)
+//      that is merged into a global table hashed with Eq. 4; the global table
+//      counts distinct keys and raises the overflow guard when they exceed
+//      L = C/2 (Eq. 6, Alg. 4)
+//   3  the K' (key, count) pairs are put in key order and their counts
+//      exclusive-scanned (Alg. 4): for K' <= 4096 every CTA computes, for its
+//      share of the pairs, the rank and the run offset directly (number of
+//      smaller keys and the sum of their counts); larger K' go through an LSD
+//      radix sort followed by a two-level scan
 //   4  emit: every output tile looks up its runs and writes them with 16-byte
 //      streaming stores (the paper's fill_n per pair)
 //   R  radix fallback (the paper's pdqsort: 2*K_hat > N, or the guard fired):
@@ -24,10 +28,9 @@
 // Columns with N < 2048 are sorted by a single CTA in shared memory
 // (Table 2: "sampling does not amortize").
 //
-// All device waits (grid barrier, look-back) are bounded by a timeout; a wait
-// that runs out records kDevTimeout and the launch ends early.
-
-#include <cstdio>
+// All device waits (grid barrier, mbarriers, look-back) are bounded by a
+// timeout; a wait that runs out records kDevTimeout and the launch ends early
+// after draining its own bulk copies.
 
 #include "cafs_device.cuh"
 #include "cafs_internal.h"
@@ -35,52 +38,119 @@
 namespace cafs {
 
 // ---------------------------------------------------------------------------
-// Phase 0: sampler, spectrum, Chao1, Eq. 6, provisional dispatch (CTA 0).
+// Phase 0: sampler, spectrum, Chao1, Eq. 6, provisional dispatch (one CTA).
 // ---------------------------------------------------------------------------
 template <typename K>
 __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem) {
   using T = KeyTraits<K>;
-  long long* s = reinterpret_cast<long long*>(smem);           // 1024 samples
-  int* wcount = reinterpret_cast<int*>(s + kSamples);           // 32 warp counts
+  // Algorithm 2's FreqSet: a 4096-slot open-addressing table in shared
+  // memory, filled with the 1024 strided samples in parallel.  The empty
+  // marker is the type minimum; samples equal to it are counted on the side.
+  constexpr int kFreqSlots = 4096;
+  long long* fkey = reinterpret_cast<long long*>(smem);                 // kFreqSlots
+  unsigned* fcnt = reinterpret_cast<unsigned*>(fkey + kFreqSlots);      // kFreqSlots
+  long long* s = reinterpret_cast<long long*>(fcnt + kFreqSlots);       // kSamples, position order
+  int* scratch = reinterpret_cast<int*>(s + kSamples);                  // kWarps + 2
   const int t = threadIdx.x;
   const unsigned long long n = p.n;
   const unsigned long long stride = n / kSamples > 0 ? n / kSamples : 1ull;
   const int ns = n < (unsigned long long)kSamples ? (int)n : kSamples;
+  const long long kmin = (long long)T::min_key();
 
-  long long v = LLONG_MAX;
-  if (t < ns) v = (long long)keys[(unsigned long long)t * stride];
-  s[t] = v;
+  for (int i = t; i < kFreqSlots; i += kThreads) {
+    fkey[i] = kmin;
+    fcnt[i] = 0u;
+  }
+  if (t == 0) scratch[kWarps] = 0;        // samples equal to the type minimum
+  if (t == 0) scratch[kWarps + 1] = 0;    // next free index in the distinct list
+  for (int i = t; i < kSamples; i += kThreads)
+    s[i] = i < ns ? (long long)keys[(unsigned long long)i * stride] : LLONG_MAX;
   __syncthreads();
-  int asc = (t + 1 < ns) ? (s[t] <= s[t + 1]) : 1;
+  int asc = 1;
+  for (int i = t; i + 1 < ns; i += kThreads) asc &= (s[i] <= s[i + 1]);
   const int hint = __syncthreads_and(asc);
 
-  // Sort the samples; runs of equal values give the frequency spectrum.
-  bitonic_sort_pairs(s, nullptr, kSamples);
-  const int start = (t < ns) && (t == 0 || s[t] != s[t - 1]);
-  int len = 0;
-  if (start) {
-    len = 1;
-    while (t + len < ns && s[t + len] == s[t]) ++len;
+  // Linear-probe insert (Alg. 2), load <= 1/4.
+  for (int i = t; i < ns; i += kThreads) {
+    const long long x = s[i];
+    if (x == kmin) {
+      atomicAdd(scratch + kWarps, 1);
+      continue;
+    }
+    unsigned slot = (unsigned)hash_slot((unsigned long long)x, 12);
+    for (int probe = 0; probe < kFreqSlots; ++probe, slot = (slot + 1) & (kFreqSlots - 1)) {
+      const long long k = *reinterpret_cast<volatile long long*>(fkey + slot);
+      if (k == x) break;
+      if (k == kmin) {
+        const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(fkey + slot),
+                                                   (unsigned long long)kmin, (unsigned long long)x);
+        if (old == kmin || old == x) break;
+      }
+    }
+    atomicAdd(fcnt + slot, 1u);
   }
-  const int u = __syncthreads_count(start);
-  const int f1 = __syncthreads_count(start && len == 1);
-  const int f2 = __syncthreads_count(start && len == 2);
-
-  // The u <= 8 distinct sample values, ascending (kept for the tiny path).
-  const unsigned ballot = __ballot_sync(0xffffffffu, start);
-  if ((t & 31) == 0) wcount[t >> 5] = __popc(ballot);
   __syncthreads();
+  // Spectrum: occupied slots (u), slots seen once (f1) and twice (f2).
+  int cu = 0, c1 = 0, c2 = 0;
+  for (int i = t; i < kFreqSlots; i += kThreads) {
+    const unsigned c = fcnt[i];
+    cu += c > 0u;
+    c1 += c == 1u;
+    c2 += c == 2u;
+  }
+  const int nmin = scratch[kWarps];
+  int u = block_sum(cu, scratch) + (nmin > 0);
+  const int f1 = block_sum(c1, scratch) + (nmin == 1);
+  const int f2 = block_sum(c2, scratch) + (nmin == 2);
+
+  // The distinct sample values (unordered): all of them go to the workspace
+  // (they seed the count tables), and when u <= 8 also to the record (tiny
+  // path).
   Record& r = p.ctrl->rec;
-  if (start && u <= kTinyMax) {
-    int rank = __popc(ballot & lanemask_lt());
-    for (int w = 0; w < (t >> 5); ++w) rank += wcount[w];
-    r.tiny_keys[rank] = s[t];
+  for (int i = t; i < kFreqSlots + 1; i += kThreads) {
+    const bool occupied = i < kFreqSlots ? fcnt[i] > 0u : nmin > 0;
+    if (occupied) {
+      const long long v = i < kFreqSlots ? fkey[i] : kmin;
+      const int idx = atomicAdd(scratch + kWarps + 1, 1);
+      if (p.sample_keys) p.sample_keys[idx] = v;
+      if (u <= kTinyMax) r.tiny_keys[idx] = v;
+    }
+  }
+  // Tiny path: find an odd multiplier that sends the u <= 8 sampled keys to
+  // distinct buckets (Eq. 4's multiplicative hash with other multipliers).
+  __syncthreads();
+  if (u <= kTinyMax && t < 32) {
+    unsigned long long tkv[kTinyMax];
+    #pragma unroll
+    for (int j = 0; j < kTinyMax; ++j)
+      tkv[j] = j < u ? (unsigned long long)(typename T::U)(K)r.tiny_keys[j] : 0ull;
+    bool found = false;
+    for (int round = 0; round < 16 && !found; ++round) {
+      const unsigned long long m = (kPhi * (2ull * (unsigned long long)(round * 32 + t) + 1ull)) | 1ull;
+      unsigned mask = 0;
+      bool ok = true;
+      #pragma unroll
+      for (int j = 0; j < kTinyMax; ++j) {
+        if (j < u) {
+          const unsigned b = (unsigned)((tkv[j] * m) >> (64 - kTinyBucketBits));
+          ok = ok && !((mask >> b) & 1u);
+          mask |= 1u << b;
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      if (bal) {
+        if (t == __ffs(bal) - 1) {
+          r.tiny_mult = m;
+          r.tiny_hash_ok = 1;
+        }
+        found = true;
+      }
+    }
   }
   if (t == 0) {
     const bool saturated = (u == kSamples);
-    unsigned long long k_hat = saturated
-        ? n
-        : (unsigned long long)u + ((unsigned long long)f1 * f1) / (2ull * (f2 + 1));
+    const unsigned long long k_hat =
+        saturated ? n : (unsigned long long)u + ((unsigned long long)f1 * f1) / (2ull * (f2 + 1));
     const unsigned long long cap = T::kCap;
     unsigned long long m = bit_ceil_u64((8ull * k_hat) / cap);
     if (m < 8) m = 8;
@@ -100,62 +170,163 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
     r.sample_nondecreasing = hint;
     r.n_tiny = u <= kTinyMax ? u : 0;
     int d;
-    if (k_hat <= (unsigned long long)kTinyMax && u <= kTinyMax) d = 3;          // TINY
-    else if (2ull * k_hat > n) d = 5;                                          // HIGH_ENTROPY
-    else d = 4;                                                                // MAIN
+    if (k_hat <= (unsigned long long)kTinyMax && u <= kTinyMax) d = 3;   // TINY
+    else if (2ull * k_hat > n) d = 5;                                   // HIGH_ENTROPY
+    else d = 4;                                                         // MAIN
     r.dispatch = d;
     r.path = d;
   }
   __syncthreads();
 }
 
+// Geometry of one CTA's share of a column: `head` scalar elements before the
+// first 16-byte boundary, then whole 16-byte vectors [v0, v1) of this CTA,
+// then the ragged tail [tail0, n) handled by the last CTA.
+template <typename K>
+struct Share {
+  unsigned long long head, nvec, tail0, v0, v1;
+  __device__ Share(const K* keys, unsigned long long n) {
+    constexpr int VPE = KeyTraits<K>::kVec;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+    head = ((16u - (addr & 15u)) & 15u) / sizeof(K);
+    if (head > n) head = n;
+    nvec = (n - head) / VPE;
+    tail0 = head + nvec * VPE;
+    const unsigned nb = gridDim.x, b = blockIdx.x;
+    v0 = nvec * b / nb;
+    v1 = nvec * (b + 1) / nb;
+  }
+};
+
 // ---------------------------------------------------------------------------
-// Element iteration over one CTA's contiguous share of a column, with 16-byte
-// vector loads on the aligned interior and scalar loads on the ragged ends.
+// The bulk-copy ring: this CTA's vectors of the column stream through
+// kRingStages chunks of shared memory.  Warp kConsumerWarps (the last) issues
+// cp.async.bulk copies, warps 0..kConsumerWarps-1 consume.  start() issues the
+// first kRingStages chunks (at launch, before the sampler's grid barrier);
+// run() streams the whole share through a counting functor; drain() waits for
+// copies that will not be consumed.  Every wait is bounded.
 // ---------------------------------------------------------------------------
-template <typename K, int U, typename F>
-__device__ __forceinline__ void for_each_key(const K* keys, unsigned long long n, F&& f,
-                                             const unsigned* abort_flag) {
-  using T = KeyTraits<K>;
-  using V = typename T::Vec;
-  constexpr int VPE = T::kVec;
-  const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
-  unsigned long long head = ((16u - (addr & 15u)) & 15u) / sizeof(K);
-  if (head > n) head = n;
-  const unsigned long long nvec = (n - head) / VPE;
-  const unsigned long long tail0 = head + nvec * VPE;
-  const unsigned nb = gridDim.x, b = blockIdx.x;
-  if (b == 0)
-    for (unsigned long long i = threadIdx.x; i < head; i += blockDim.x) f(keys[i]);
-  if (b == nb - 1)
-    for (unsigned long long i = tail0 + threadIdx.x; i < n; i += blockDim.x) f(keys[i]);
-  const unsigned long long v0 = nvec * b / nb, v1 = nvec * (b + 1) / nb;
-  const V* vp = reinterpret_cast<const V*>(keys + head);
-  for (unsigned long long base = v0; base < v1; base += (unsigned long long)kThreads * U) {
-    if (abort_flag) {
-      unsigned a = 0;
-      if ((threadIdx.x & 31) == 0) a = ld_relaxed_u32(abort_flag);
-      a = __shfl_sync(0xffffffffu, a, 0);
-      if (a) break;
+template <typename K>
+struct Ring {
+  unsigned char* buf;           // kRingBytes
+  unsigned long long* full;     // kRingStages
+  unsigned long long* empty;    // kRingStages
+  const unsigned char* src;     // first byte of this CTA's vector range
+  unsigned long long total;     // bytes of this CTA's vector range
+  unsigned long long nchunks;
+  unsigned long long issued;    // producer lane only
+  bool live;
+
+  __device__ __forceinline__ bool producer() const {
+    return threadIdx.x == kConsumerWarps * 32;
+  }
+
+  __device__ void start(const Params& p, const K* keys, unsigned char* smem) {
+    const Share<K> sh(keys, p.n);
+    buf = smem + (kPipelineSmem - kRingBytes);
+    full = reinterpret_cast<unsigned long long*>(buf - 128);
+    empty = full + kRingStages;
+    src = reinterpret_cast<const unsigned char*>(keys + sh.head) + sh.v0 * 16ull;
+    total = (sh.v1 - sh.v0) * 16ull;
+    nchunks = (total + kChunkBytes - 1) / kChunkBytes;
+    issued = 0;
+    live = true;
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kRingStages; ++s) {
+        mbar_init(full + s, 1);
+        mbar_init(empty + s, kConsumerWarps);
+      }
+      fence_mbar_init();
     }
-    V buf[U];
-    #pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const unsigned long long v = base + (unsigned long long)j * kThreads + threadIdx.x;
-      if (v < v1) buf[j] = __ldcs(vp + v);
+    __syncthreads();
+    if (producer())
+      while (issued < nchunks && issued < (unsigned long long)kRingStages) issue(issued++);
+  }
+
+  __device__ __forceinline__ unsigned bytes_of(unsigned long long ch) const {
+    const unsigned long long off = ch * (unsigned long long)kChunkBytes;
+    return (unsigned)((total - off) < (unsigned long long)kChunkBytes ? (total - off) : kChunkBytes);
+  }
+
+  __device__ __forceinline__ void issue(unsigned long long ch) {
+    const int s = (int)(ch % kRingStages);
+    const unsigned bytes = bytes_of(ch);
+    mbar_arrive_expect_tx(full + s, bytes);
+    bulk_g2s(buf + (size_t)s * kChunkBytes, src + ch * (unsigned long long)kChunkBytes, bytes, full + s);
+  }
+
+  // Waits for the copies that may still be in flight (the last kRingStages
+  // issued chunks; every earlier chunk was consumed before its stage was
+  // reused), then retires the barriers.
+  __device__ void drain(const Params& p) {
+    if (!live) return;
+    if (producer()) {
+      const unsigned long long first = issued > (unsigned long long)kRingStages ? issued - kRingStages : 0ull;
+      for (unsigned long long ch = first; ch < issued; ++ch)
+        mbar_wait(full + (ch % kRingStages), (unsigned)(ch / kRingStages) & 1u, p.timeout_ns, p.ctrl);
     }
-    #pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const unsigned long long v = base + (unsigned long long)j * kThreads + threadIdx.x;
-      if (v < v1) {
-        K e[VPE];
-        unpack(buf[j], e);
-        #pragma unroll
-        for (int q = 0; q < VPE; ++q) f(e[q]);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int s = 0; s < kRingStages; ++s) {
+        mbar_inval(full + s);
+        mbar_inval(empty + s);
+      }
+    __syncthreads();
+    live = false;
+  }
+
+  // Streams the whole share; consumers call f.chunk() on each chunk and
+  // f.single() on the scalar head/tail elements.  When `*skip` becomes
+  // non-zero the consumers stop counting (the stream still runs to its end).
+  template <typename F>
+  __device__ bool run(const Params& p, const K* keys, const unsigned* skip, F& f) {
+    using T = KeyTraits<K>;
+    constexpr int VPE = T::kVec;
+    constexpr int kConsumers = kConsumerWarps * 32;
+    Ctrl* c = p.ctrl;
+    const unsigned long long n = p.n;
+    const Share<K> sh(keys, n);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool consumer = warp < kConsumerWarps;
+    const int ctid = threadIdx.x;
+    if (consumer) {
+      if (blockIdx.x == 0)
+        for (unsigned long long i = ctid; i < sh.head; i += kConsumers) f.single(keys[i]);
+      if (blockIdx.x == gridDim.x - 1)
+        for (unsigned long long i = sh.tail0 + ctid; i < n; i += kConsumers) f.single(keys[i]);
+    }
+    bool ok = true;
+    if (!consumer) {
+      if (producer()) {
+        for (; issued < nchunks; ++issued) {
+          const int s = (int)(issued % kRingStages);
+          const unsigned k = (unsigned)(issued / kRingStages);
+          if (!mbar_wait(empty + s, (k - 1) & 1u, p.timeout_ns, c)) { ok = false; break; }
+          issue(issued);
+        }
+      }
+    } else {
+      for (unsigned long long ch = 0; ch < nchunks; ++ch) {
+        const int s = (int)(ch % kRingStages);
+        const unsigned k = (unsigned)(ch / kRingStages);
+        if (!mbar_wait(full + s, k & 1u, p.timeout_ns, c)) { ok = false; break; }
+        unsigned sk = 0;
+        if (lane == 0) sk = skip ? ld_relaxed_u32(skip) : 0u;
+        sk = __shfl_sync(0xffffffffu, sk, 0);
+        if (!sk) {
+          const unsigned nk = bytes_of(ch) / (unsigned)sizeof(K);
+          const K* ck = reinterpret_cast<const K*>(buf + (size_t)s * kChunkBytes);
+          constexpr int KPT = kVecsPerThread * VPE;
+          f.template chunk<KPT, kConsumers>(ck + ctid, nk > (unsigned)ctid ? (nk - ctid + kConsumers - 1) / kConsumers : 0u);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
       }
     }
+    drain(p);
+    return ok && !device_failed(c);
   }
-}
+};
 
 // ---------------------------------------------------------------------------
 // Phase 1: IsMonotone (Alg. 3) over the whole column; early exit on the
@@ -204,30 +375,51 @@ __device__ void grid_copy(const K* src, K* dst, unsigned long long n) {
 // of an empty slot increments the occupancy counter and records the slot; the
 // guard fires once more than L slots are claimed or the table is full.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void global_insert(const Params& p, unsigned long long key64,
-                                              unsigned inc, int logC, unsigned long long C,
-                                              unsigned long long L) {
-  Ctrl* c = p.ctrl;
-  const unsigned long long mask = C - 1;
-  const unsigned long long h = hash_slot(key64, logC);
-  for (unsigned long long probe = 0; probe < C; ++probe) {
+struct GlobalTable {
+  unsigned long long* keys;
+  unsigned* counts;
+  unsigned* claimed;
+  Ctrl* ctrl;
+  unsigned long long C, L;
+  int logC;
+};
+
+__device__ __forceinline__ GlobalTable global_table(const Params& p) {
+  GlobalTable g;
+  g.keys = p.tkeys;
+  g.counts = p.tcounts;
+  g.claimed = p.claimed;
+  g.ctrl = p.ctrl;
+  g.C = p.ctrl->rec.C;
+  g.L = p.ctrl->rec.L;
+  g.logC = log2_pow2(g.C);
+  return g;
+}
+
+__device__ __noinline__ void global_insert(GlobalTable g, unsigned long long key64, unsigned inc) {
+  Ctrl* c = g.ctrl;
+  const unsigned long long mask = g.C - 1;
+  const unsigned long long h = hash_slot(key64, g.logC);
+  for (unsigned long long probe = 0; probe < g.C; ++probe) {
+    // Once the guard has fired the counts are discarded: stop probing.
+    if ((probe & 15ull) == 15ull && ld_relaxed_u32(&c->overflow)) return;
     const unsigned long long slot = (h + probe) & mask;
-    const unsigned long long k = ld_relaxed_u64(p.tkeys + slot);
+    const unsigned long long k = ld_relaxed_u64(g.keys + slot);
     if (k == key64) {
-      atomicAdd(p.tcounts + slot, inc);
+      atomicAdd(g.counts + slot, inc);
       return;
     }
     if (k == kEmpty64) {
-      const unsigned long long old = atomicCAS(p.tkeys + slot, kEmpty64, key64);
+      const unsigned long long old = atomicCAS(g.keys + slot, kEmpty64, key64);
       if (old == kEmpty64) {
         const unsigned idx = atomicAdd(&c->occupancy, 1u);
-        if (idx < C) p.claimed[idx] = (unsigned)slot;
-        atomicAdd(p.tcounts + slot, inc);
-        if (idx >= L) atomicExch(&c->overflow, 1u);
+        if (idx < g.C) g.claimed[idx] = (unsigned)slot;
+        atomicAdd(g.counts + slot, inc);
+        if (idx >= g.L) atomicExch(&c->overflow, 1u);
         return;
       }
       if (old == key64) {
-        atomicAdd(p.tcounts + slot, inc);
+        atomicAdd(g.counts + slot, inc);
         return;
       }
     }
@@ -238,151 +430,309 @@ __device__ __forceinline__ void global_insert(const Params& p, unsigned long lon
 // ---------------------------------------------------------------------------
 // Phase 2: count (tiny or main).
 // ---------------------------------------------------------------------------
+
+// The CTA's shared counting table: NB buckets of kBucketSlots keys (16 bytes
+// of int32 keys or 32 bytes of int64 keys per bucket, Sec. 4.2's one-line
+// bucket), each slot with R counter replicas (lane % R) so that lanes of a
+// warp hitting the same key do not serialise.  Passed by value to the
+// non-inlined slow path so that the hot loop stays small.
+// Slots per bucket: one 16-byte shared-memory load reads a whole bucket.
 template <typename K>
-__device__ void phase_count(const Params& p, const K* keys, unsigned char* smem, bool tiny) {
+constexpr int bucket_slots() { return 16 / (int)sizeof(K); }
+
+template <typename K>
+struct LocalTable {
+  static constexpr int kBucketSlots = bucket_slots<K>();
+  K* keys;          // NB * kBucketSlots, bucket-major; nullptr: no shared table
+  unsigned* cnt;    // NB * kBucketSlots * R
+  unsigned* occ;    // distinct keys held
+  unsigned limit;   // at most this many distinct keys (half the slots)
+  int logNB, NB, R, lane_rep;
+  GlobalTable gt;
+
+  __device__ __forceinline__ unsigned home(K x) const {
+    return (unsigned)hash_slot((unsigned long long)(typename KeyTraits<K>::U)x, logNB);
+  }
+  __device__ __forceinline__ void add(unsigned slot) const {
+    atomicAdd(cnt + slot * R + lane_rep, 1u);
+  }
+};
+
+// Reads the keys of one bucket with a single 16-byte load.
+__device__ __forceinline__ void load_bucket(const long long* kb, long long* k) {
+  const longlong2 a = *reinterpret_cast<const longlong2*>(kb);
+  k[0] = a.x; k[1] = a.y;
+}
+__device__ __forceinline__ void load_bucket(const int* kb, int* k) {
+  const int4 a = *reinterpret_cast<const int4*>(kb);
+  k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+}
+
+// Slow path of one key (not the type minimum) that is not in its home
+// bucket: scan buckets from home (linear probing over buckets); a key lives
+// in the first bucket that had a free slot when it was inserted, so the scan
+// stops at the first bucket with a free slot.  Claims that slot while the
+// table holds fewer than `limit` distinct keys, else goes to the global table.
+// `inc` is 0 when the table is being seeded with the sampled keys.
+template <typename K>
+__device__ __forceinline__ void slow_insert(K x, const LocalTable<K>& t, unsigned inc) {
+  using T = KeyTraits<K>;
+  constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
+  const K kmin = T::min_key();
+  if (t.keys) {
+    unsigned b = t.home(x);
+    for (int probe = 0; probe < t.NB; ++probe, b = (b + 1) & (unsigned)(t.NB - 1)) {
+      for (int j = 0; j < kBucketSlots; ++j) {
+        K* slotp = t.keys + b * kBucketSlots + j;
+        const K k = *reinterpret_cast<volatile K*>(slotp);
+        if (k == x) {
+          if (inc) t.add(b * kBucketSlots + j);
+          return;
+        }
+        if (k == kmin) {
+          if (*reinterpret_cast<volatile unsigned*>(t.occ) >= t.limit) {
+            if (inc) global_insert(t.gt, (unsigned long long)(long long)x, inc);
+            return;
+          }
+          K old;
+          if constexpr (sizeof(K) == 8) {
+            old = (K)atomicCAS(reinterpret_cast<unsigned long long*>(slotp),
+                               (unsigned long long)kmin, (unsigned long long)x);
+          } else {
+            old = (K)atomicCAS(reinterpret_cast<unsigned*>(slotp), (unsigned)kmin, (unsigned)x);
+          }
+          if (old == kmin) atomicAdd(t.occ, 1u);
+          if (old == kmin || old == x) {
+            if (inc) t.add(b * kBucketSlots + j);
+            return;
+          }
+          // another key took the slot: carry on with the next one
+        }
+      }
+    }
+  }
+  if (inc) global_insert(t.gt, (unsigned long long)(long long)x, inc);
+}
+
+// Per-key counting of one thread.  TINY: the <= 8 sampled keys are looked
+// up through a collision-free multiplicative hash into kTinyBuckets buckets
+// and counted in this thread's own shared-memory counters (Sec. 4.4, the
+// paper's eight branchless counters).  Main path (and tiny misses): read the
+// key's home bucket and add to the matching slot's counter (Sec. 4.2's bucket
+// update).  Keys that miss are handled afterwards in one loop per chunk, so
+// that a warp's misses at different positions share one pass of the slow
+// path.  Keys equal to the type minimum (the tables' empty marker) are only
+// counted.
+template <typename K, bool TINY>
+struct KeyCounter {
+  using T = KeyTraits<K>;
+  LocalTable<K> lt;
+  // tiny path
+  unsigned long long tmult;
+  unsigned tvalid;
+  const K* tkey;        // kTinyBuckets keys by bucket
+  unsigned* tcnt;       // this thread's counters, stride kConsumerWarps*32
+  unsigned long long special;
+
+  // Fast path; returns false when the key must take the slow path.
+  __device__ __forceinline__ bool fast(K x) {
+    if constexpr (TINY) {
+      const unsigned long long ux = (unsigned long long)(typename T::U)x;
+      const unsigned b = (unsigned)((ux * tmult) >> (64 - kTinyBucketBits));
+      if (((tvalid >> b) & 1u) && tkey[b] == x) {
+        tcnt[b * (kConsumerWarps * 32)] += 1u;
+        return true;
+      }
+    }
+    if (x == T::min_key()) {
+      ++special;
+      return true;
+    }
+    if (!TINY && lt.keys) {
+      constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
+      const unsigned b = lt.home(x);
+      K k[kBucketSlots];
+      load_bucket(lt.keys + b * kBucketSlots, k);
+      int hit = -1;
+      #pragma unroll
+      for (int j = kBucketSlots - 1; j >= 0; --j)
+        if (k[j] == x) hit = j;
+      if (hit >= 0) {
+        lt.add(b * kBucketSlots + hit);
+        return true;
+      }
+    }
+    return false;
+  }
+
+  __device__ __forceinline__ void single(K x) {
+    if (!fast(x)) slow_insert<K>(x, lt, 1u);
+  }
+
+  // Keys src[0], src[STRIDE], ..., src[(cnt-1)*STRIDE] (cnt <= B) of a chunk
+  // in shared memory.
+  template <int B, int STRIDE>
+  __device__ __forceinline__ void chunk(const K* src, unsigned cnt) {
+    unsigned miss = 0;
+    #pragma unroll
+    for (int i = 0; i < B; ++i)
+      if ((unsigned)i < cnt && !fast(src[i * STRIDE])) miss |= 1u << i;
+    while (miss) {
+      const int i = __ffs(miss) - 1;
+      miss &= miss - 1;
+      slow_insert<K>(src[i * STRIDE], lt, 1u);
+    }
+  }
+};
+
+// Adds this CTA's count of type-minimum keys to the control block.
+__device__ __forceinline__ void special_out(Ctrl* c, unsigned long long special, unsigned long long* red) {
+  const unsigned long long bs = block_sum(special, red);
+  if (threadIdx.x == 0 && bs) atomicAdd(&c->special, bs);
+}
+
+template <typename K, bool TINY>
+__device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem, Ring<K>& ring) {
   using T = KeyTraits<K>;
   Ctrl* c = p.ctrl;
   const Record& r = c->rec;
-  const unsigned long long C = r.C, L = r.L;
-  const int logC = log2_pow2(C);
   const unsigned long long k_hat = r.k_hat;
   const K kmin = T::min_key();
+  constexpr int kConsumers = kConsumerWarps * 32;
 
-  // Per-CTA shared table: S slots (power of two) with R privatised counter
-  // replicas per slot (lane % R) so that hot keys do not serialise a warp.
+  // Per-CTA shared table: S slots (power of two, load <= 1/4 when K_hat is
+  // right) with R privatised counter replicas per slot (lane % R) so that hot
+  // keys do not serialise a warp's atomics.
   constexpr int kKeyBytes = sizeof(K);
-  const int budget = kPipelineSmem - 4096;
-  int S = 256;
+  int S = 256;   // slots = buckets * slots per bucket; load <= 1/4 when K_hat is right
   while (S < kLocalSlotsMax && (unsigned long long)S < 4ull * k_hat) S <<= 1;
-  while (S > 256 && S * (kKeyBytes + 4) > budget) S >>= 1;
+  const int budget = S <= 2048 ? kSmallTableBytes : kLocalTableBytes;
   int R = 32;
   while (R > 1 && S * (kKeyBytes + 4 * R) > budget) R >>= 1;
-  const bool use_local = tiny || (k_hat <= (unsigned long long)(kLocalSlotsMax / 2));
-  const int logS = log2_pow2(S);
-  const unsigned limit = S / 2;
+  const bool use_local = TINY || (k_hat <= (unsigned long long)kLocalSlotsMax);
 
-  K* lkeys = reinterpret_cast<K*>(smem);
-  unsigned* lcnt = reinterpret_cast<unsigned*>(smem + (size_t)S * kKeyBytes);
-  unsigned* misc = reinterpret_cast<unsigned*>(smem + (size_t)S * (kKeyBytes + 4 * R));
-  unsigned* local_occ = misc;                                          // 1
-  unsigned long long* tiny_tot = reinterpret_cast<unsigned long long*>(misc + 2);  // 8
-  unsigned long long* red = tiny_tot + kTinyMax;                        // kWarps
+  // Shared memory: table (| tiny counters) | misc ... barriers | ring (top).
+  const int table_bytes = TINY ? kTinyTableBytes + kTinyBuckets * kConsumers * 4
+                               : (use_local ? S * (kKeyBytes + 4 * R) : 0);
+  unsigned char* tbase = smem;
+  K* lkeys = reinterpret_cast<K*>(tbase);
+  unsigned* lcnt = reinterpret_cast<unsigned*>(tbase + (size_t)S * kKeyBytes);
+  unsigned* tcnt = reinterpret_cast<unsigned*>(tbase + kTinyTableBytes);           // kTinyBuckets x kConsumers
+  unsigned char* mbase = smem + table_bytes;
+  unsigned* local_occ = reinterpret_cast<unsigned*>(mbase);                       // 1
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(mbase + 8);     // kWarps
+  K* tkey = reinterpret_cast<K*>(mbase + 8 + 8 * kWarps);                          // kTinyBuckets
+  static_assert(kLocalTableBytes + kMiscBytes + 128 <= kPipelineSmem - kRingBytes, "table under ring");
+  static_assert(kTinyTableBytes + kTinyBuckets * kConsumerWarps * 32 * 4 + kMiscBytes + 128 <=
+                    kPipelineSmem - kRingBytes, "tiny table under ring");
 
+  const int nt = r.n_tiny;
+  const bool tiny_hash = TINY && r.tiny_hash_ok;
+  const unsigned long long tmult = r.tiny_mult;
+  unsigned tvalid = 0;
+  if (tiny_hash) {
+    for (int j = 0; j < nt; ++j) {
+      const K kj = (K)r.tiny_keys[j];
+      tvalid |= 1u << (unsigned)(((unsigned long long)(typename T::U)kj * tmult) >> (64 - kTinyBucketBits));
+    }
+  }
   if (use_local) {
     for (int i = threadIdx.x; i < S; i += blockDim.x) lkeys[i] = kmin;
     for (int i = threadIdx.x; i < S * R; i += blockDim.x) lcnt[i] = 0u;
   }
+  if (tiny_hash) {
+    for (int i = threadIdx.x; i < kTinyBuckets * kConsumers; i += blockDim.x) tcnt[i] = 0u;
+    if (threadIdx.x < nt) {
+      const K kj = (K)r.tiny_keys[threadIdx.x];
+      tkey[((unsigned long long)(typename T::U)kj * tmult) >> (64 - kTinyBucketBits)] = kj;
+    }
+  }
   if (threadIdx.x == 0) *local_occ = 0u;
-  if (threadIdx.x < kTinyMax) tiny_tot[threadIdx.x] = 0ull;
   __syncthreads();
-
-  const int nt = tiny ? r.n_tiny : 0;
-  K tk[kTinyMax];
-  #pragma unroll
-  for (int j = 0; j < kTinyMax; ++j) tk[j] = (K)r.tiny_keys[j < nt ? j : 0];
-  unsigned tc[kTinyMax];
-  #pragma unroll
-  for (int j = 0; j < kTinyMax; ++j) tc[j] = 0u;
-  unsigned long long special = 0, miss = 0;
-  const int lane_rep = (threadIdx.x & 31) & (R - 1);
-
-  auto local_insert = [&](K x) -> bool {
-    const unsigned long long ux = (unsigned long long)(typename T::U)x;
-    const unsigned long long h = hash_slot(ux, logS);
-    bool reserved = false;
-    for (int probe = 0; probe < S; ++probe) {
-      const int slot = (int)((h + probe) & (unsigned long long)(S - 1));
-      const K k = *reinterpret_cast<volatile K*>(lkeys + slot);
-      if (k == x) {
-        atomicAdd(lcnt + slot * R + lane_rep, 1u);
-        return true;
-      }
-      if (k == kmin) {
-        if (!reserved) {
-          if (atomicAdd(local_occ, 1u) >= limit) return false;
-          reserved = true;
-        }
-        K old;
-        if constexpr (sizeof(K) == 8) {
-          old = (K)atomicCAS(reinterpret_cast<unsigned long long*>(lkeys + slot),
-                             (unsigned long long)kmin, (unsigned long long)x);
-        } else {
-          old = (K)atomicCAS(reinterpret_cast<unsigned*>(lkeys + slot), (unsigned)kmin,
-                             (unsigned)x);
-        }
-        if (old == kmin || old == x) {
-          atomicAdd(lcnt + slot * R + lane_rep, 1u);
-          return true;
-        }
-      }
+  if (!TINY && use_local) {
+    // Seed with the distinct sampled keys (counts 0), so that the frequent
+    // keys are found in their buckets from the first chunk on.
+    LocalTable<K> seed;
+    seed.keys = lkeys;
+    seed.cnt = lcnt;
+    seed.occ = local_occ;
+    seed.limit = S / 2;
+    seed.NB = S / LocalTable<K>::kBucketSlots;
+    seed.logNB = log2_pow2(S / LocalTable<K>::kBucketSlots);
+    seed.R = R;
+    seed.lane_rep = 0;
+    seed.gt = global_table(p);
+    const int u = (int)r.u;
+    for (int j = threadIdx.x; j < u; j += blockDim.x) {
+      const K kj = (K)__ldcg(p.sample_keys + j);
+      if (kj != kmin) slow_insert<K>(kj, seed, 0u);
     }
-    return false;
-  };
+    __syncthreads();
+  }
 
-  auto process = [&](K x) {
-    if (tiny) {
-      bool hit = false;
-      #pragma unroll
-      for (int j = 0; j < kTinyMax; ++j) {
-        const bool e = (j < nt) && (x == tk[j]);
-        tc[j] += e ? 1u : 0u;
-        hit |= e;
+  const bool ok = [&]() {
+    LocalTable<K> lt;
+    lt.keys = use_local ? lkeys : nullptr;
+    lt.cnt = lcnt;
+    lt.occ = local_occ;
+    lt.limit = S / 2;
+    lt.NB = S / LocalTable<K>::kBucketSlots;
+    lt.logNB = log2_pow2(S / LocalTable<K>::kBucketSlots);
+    lt.R = R;
+    lt.lane_rep = (threadIdx.x & 31) & (R - 1);
+    lt.gt = global_table(p);
+    if (tiny_hash) {
+      KeyCounter<K, true> kc;
+      kc.lt = lt;
+      kc.tmult = tmult;
+      kc.tvalid = tvalid;
+      kc.tkey = tkey;
+      kc.tcnt = tcnt + (threadIdx.x < kConsumers ? threadIdx.x : 0);
+      kc.special = 0;
+      const bool res = ring.run(p, keys, &c->overflow, kc);
+      // Tiny buckets: add up the per-thread counters, insert each sampled key.
+      for (int j = 0; j < nt; ++j) {
+        const K kj = (K)r.tiny_keys[j];
+        const unsigned b = (unsigned)(((unsigned long long)(typename T::U)kj * tmult) >> (64 - kTinyBucketBits));
+        const unsigned long long v = threadIdx.x < kConsumers ? tcnt[b * kConsumers + threadIdx.x] : 0u;
+        const unsigned long long tot = block_sum(v, red);
+        if (threadIdx.x == 0 && tot) {
+          if (kj == kmin) kc.special += tot;
+          else global_insert(lt.gt, (unsigned long long)(long long)kj, (unsigned)tot);
+        }
       }
-      if (hit) return;
-      ++miss;
+      special_out(c, kc.special, red);
+      return res;
     }
-    if (x == kmin) {
-      ++special;
-      return;
-    }
-    if (use_local && local_insert(x)) return;
-    global_insert(p, (unsigned long long)(long long)x, 1u, logC, C, L);
-  };
-
-  for_each_key<K, 4>(keys, p.n, process, &c->overflow);
-  __syncthreads();
+    KeyCounter<K, false> kc;
+    kc.lt = lt;
+    kc.special = 0;
+    const bool res = ring.run(p, keys, &c->overflow, kc);
+    special_out(c, kc.special, red);
+    return res;
+  }();
 
   // Flush the shared table into the global table.
   if (use_local) {
+    const GlobalTable g = global_table(p);
     for (int i = threadIdx.x; i < S; i += blockDim.x) {
       const K k = lkeys[i];
       if (k != kmin) {
         unsigned tot = 0;
         for (int q = 0; q < R; ++q) tot += lcnt[i * R + q];
-        if (tot) global_insert(p, (unsigned long long)(long long)k, tot, logC, C, L);
+        if (tot) global_insert(g, (unsigned long long)(long long)k, tot);
       }
     }
   }
-  if (tiny) {
-    #pragma unroll
-    for (int j = 0; j < kTinyMax; ++j) {
-      unsigned v = tc[j];
-      v = __reduce_add_sync(0xffffffffu, v);
-      if ((threadIdx.x & 31) == 0 && v) atomicAdd(tiny_tot + j, (unsigned long long)v);
-    }
-  }
-  __syncthreads();
-  if (tiny && threadIdx.x < nt) {
-    const unsigned long long tot = tiny_tot[threadIdx.x];
-    const K key = (K)r.tiny_keys[threadIdx.x];
-    if (tot) {
-      if (key == kmin) special += tot;
-      else global_insert(p, (unsigned long long)(long long)key, (unsigned)tot, logC, C, L);
-    }
-  }
-  const unsigned long long bs = block_sum(special, red);
-  const unsigned long long bm = block_sum(miss, red);
-  if (threadIdx.x == 0) {
-    if (bs) atomicAdd(&c->special, bs);
-    if (bm) atomicAdd(&c->miss, bm);
-  }
+  return ok;
 }
 
-// Reset the global-table slots claimed in this call (grid-stride).
+// Reset the global-table slots claimed in this call: this CTA's share.
 __device__ void reset_claimed(const Params& p, unsigned occ) {
-  const unsigned long long G = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (unsigned long long i = gt; i < occ; i += G) {
+  const unsigned b = blockIdx.x, nb = gridDim.x;
+  const unsigned i0 = (unsigned)((unsigned long long)occ * b / nb);
+  const unsigned i1 = (unsigned)((unsigned long long)occ * (b + 1) / nb);
+  for (unsigned i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const unsigned slot = __ldcg(p.claimed + i);
     p.tkeys[slot] = kEmpty64;
     p.tcounts[slot] = 0u;
@@ -390,53 +740,56 @@ __device__ void reset_claimed(const Params& p, unsigned occ) {
 }
 
 // ---------------------------------------------------------------------------
-// Phase 3a: K' <= kSmallPairs pairs sorted by CTA 0 in shared memory, then
-// exclusive scan of the counts.  Pads (key max, count 0) fill up to a power
-// of two; zero-count runs are skipped by the emit lookup.
+// Phase 3a (K' <= kRankPairs): rank and run offset of every pair, all CTAs.
+// Keys in the table are distinct, so pair i goes to position
+//   rank_i = #{j : key_j < key_i}   (+1 when the type minimum occurs)
+// and its run starts at
+//   off_i = sum of count_j over key_j < key_i   (+ count of the minimum).
+// This is the sorted order and the exclusive scan of Alg. 4 in one pass.
+// CTA b takes pairs [b*K'/G, (b+1)*K'/G); a warp per pair, lanes over j.
 // ---------------------------------------------------------------------------
 template <typename K>
-__device__ void phase_small_pairs(const Params& p, unsigned occ, unsigned long long special,
-                                  unsigned char* smem) {
+__device__ void phase_rank_pairs(const Params& p, unsigned occ, unsigned long long special,
+                                 unsigned char* smem) {
   using T = KeyTraits<K>;
-  Ctrl* c = p.ctrl;
-  const unsigned kp = occ + (special ? 1u : 0u);
-  const int P = (int)bit_ceil_u64(kp);
-  long long* sk = reinterpret_cast<long long*>(smem);
-  unsigned* sc = reinterpret_cast<unsigned*>(sk + kSmallPairs);
-  unsigned* scratch = sc + kSmallPairs;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    if (i < (int)occ) {
-      const unsigned slot = __ldcg(p.claimed + i);
-      sk[i] = (long long)__ldcg(p.tkeys + slot);
-      sc[i] = __ldcg(p.tcounts + slot);
-      p.tkeys[slot] = kEmpty64;
-      p.tcounts[slot] = 0u;
-    } else if (i == (int)occ && special) {
-      sk[i] = (long long)T::min_key();
-      sc[i] = (unsigned)special;
-    } else {
-      sk[i] = LLONG_MAX;
-      sc[i] = 0u;
+  const unsigned b = blockIdx.x, nb = gridDim.x;
+  const unsigned i0 = (unsigned)((unsigned long long)occ * b / nb);
+  const unsigned i1 = (unsigned)((unsigned long long)occ * (b + 1) / nb);
+  K* skeys = reinterpret_cast<K*>(p.skeys);
+  const unsigned long long add = special ? 1ull : 0ull;
+  if (b == 0 && threadIdx.x == 0) {
+    if (special) {
+      skeys[0] = T::min_key();
+      p.offsets[0] = 0u;
     }
+    p.offsets[occ + add] = (unsigned)p.n;
+  }
+  if (i1 <= i0) return;
+  long long* jk = reinterpret_cast<long long*>(smem);
+  unsigned* jc = reinterpret_cast<unsigned*>(jk + kRankPairs);
+  for (unsigned j = threadIdx.x; j < occ; j += blockDim.x) {
+    const unsigned slot = __ldcg(p.claimed + j);
+    jk[j] = (long long)__ldcg(p.tkeys + slot);
+    jc[j] = __ldcg(p.tcounts + slot);
   }
   __syncthreads();
-  bitonic_sort_pairs(sk, sc, P);
-  K* skeys = reinterpret_cast<K*>(p.skeys);
-  unsigned carry = 0;
-  for (int base = 0; base < P; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const unsigned v = i < P ? sc[i] : 0u;
-    unsigned tot;
-    const unsigned ex = block_exclusive_scan(v, scratch, &tot);
-    if (i < P) {
-      p.offsets[i] = carry + ex;
-      skeys[i] = (K)sk[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (unsigned i = i0 + warp; i < i1; i += kWarps) {
+    const long long ki = jk[i];
+    unsigned rk = 0;
+    unsigned long long off = 0;
+    for (unsigned j = lane; j < occ; j += 32) {
+      const bool lt = jk[j] < ki;
+      rk += lt ? 1u : 0u;
+      off += lt ? jc[j] : 0u;
     }
-    carry += tot;
-  }
-  if (threadIdx.x == 0) {
-    p.offsets[P] = (unsigned)p.n;
-    c->rec.n_pairs = (unsigned long long)P;
+    rk = __reduce_add_sync(0xffffffffu, rk);
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+    if (lane == 0) {
+      skeys[rk + add] = (K)ki;
+      p.offsets[rk + add] = (unsigned)(off + special);
+    }
   }
 }
 
@@ -454,7 +807,7 @@ __device__ __forceinline__ unsigned radix_digit(K k, int shift) {
 constexpr unsigned long long kFlagAgg = 1ull, kFlagIncl = 2ull;
 
 template <typename K, bool PAY>
-__device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v, K* out_k,
+__device__ void radix_pass(const Params& p, const K* in_k, const unsigned* in_v, K* out_k,
                            unsigned* out_v, unsigned long long n, int pass, unsigned tag,
                            unsigned char* smem) {
   Ctrl* c = p.ctrl;
@@ -474,12 +827,11 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
 
   // Global exclusive start of every digit for this pass.
   {
-    const unsigned v = threadIdx.x < kRadixDigits ? c->hist[pass][threadIdx.x] : 0u;
+    const unsigned v = threadIdx.x < kRadixDigits ? ld_relaxed_u32(&c->hist[pass][threadIdx.x]) : 0u;
     unsigned tot;
     const unsigned ex = block_exclusive_scan(v, scratch, &tot);
     if (threadIdx.x < kRadixDigits) dstart[threadIdx.x] = ex;
   }
-  bool ok = true;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) *s_ticket = atomicAdd(&c->tickets[pass], 1u);
@@ -487,7 +839,6 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     const unsigned long long tile = *s_ticket;
     if (tile >= ntiles) break;
     const unsigned long long base = tile * kRadixTile;
-    // zero this warp's digit counters
     for (int d = lane; d < kRadixDigits; d += 32) wcnt[w * kRadixDigits + d] = 0;
     __syncwarp();
     K key[kRadixItems];
@@ -583,10 +934,8 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
       __stcg(out_k + dst, k);
       if constexpr (PAY) __stcg(out_v + dst, stage_v[i]);
     }
-    if (device_failed(c)) { ok = false; }
   }
   __syncthreads();
-  return ok;
 }
 
 // Full LSD radix sort src -> dst (tmp as ping-pong), all CTAs.  Returns false
@@ -618,14 +967,25 @@ __device__ bool radix_sort(const Params& p, const K* src_k, const unsigned* src_
   if (!grid_sync(c, epoch, p.timeout_ns)) return false;
 
   // Plan: a pass whose digit is the same for every key changes nothing.
-  int active[NP];
-  int na = 0;
-  for (int q = 0; q < NP; ++q) {
-    bool trivial = false;
-    for (int d = 0; d < kRadixDigits; ++d)
-      if ((unsigned long long)ld_relaxed_u32(&c->hist[q][d]) == n) { trivial = true; break; }
-    if (!trivial) active[na++] = q;
+  int* triv = reinterpret_cast<int*>(smem);  // NP flags
+  int* plan = triv + 8;                      // [0] = count, [1..] = passes
+  if (threadIdx.x < NP) triv[threadIdx.x] = 0;
+  __syncthreads();
+  if (threadIdx.x < kRadixDigits)
+    for (int q = 0; q < NP; ++q)
+      if ((unsigned long long)ld_relaxed_u32(&c->hist[q][threadIdx.x]) == n) triv[q] = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int na = 0;
+    for (int q = 0; q < NP; ++q)
+      if (!triv[q]) plan[1 + na++] = q;
+    plan[0] = na;
   }
+  __syncthreads();
+  const int na = plan[0];
+  unsigned active_bits = 0;  // pass indices, 4 bits each
+  for (int a = 0; a < na; ++a) active_bits |= (unsigned)plan[1 + a] << (4 * a);
+  __syncthreads();
   // The last active pass writes dst; earlier ones alternate with tmp.  If the
   // first pass would write over its own input (in-place), every target flips
   // and a final copy tmp -> dst follows.
@@ -641,8 +1001,9 @@ __device__ bool radix_sort(const Params& p, const K* src_k, const unsigned* src_
     if (flip) to_dst = !to_dst;
     K* ok_ = to_dst ? dst_k : tmp_k;
     unsigned* ov = to_dst ? dst_v : tmp_v;
-    const unsigned tag = (p.gen << 4) | ((tag_base + (unsigned)active[a]) & 15u);
-    radix_pass<K, PAY>(p, cur_k, cur_v, ok_, ov, n, active[a], tag, smem);
+    const int pass = (int)((active_bits >> (4 * a)) & 15u);
+    const unsigned tag = (p.gen << 4) | ((tag_base + (unsigned)pass) & 15u);
+    radix_pass<K, PAY>(p, cur_k, cur_v, ok_, ov, n, pass, tag, smem);
     if (!grid_sync(c, epoch, p.timeout_ns)) return false;
     cur_k = ok_;
     cur_v = ov;
@@ -735,7 +1096,6 @@ __device__ void phase_emit(const Params& p, unsigned long long npairs, unsigned 
   unsigned* tj = reinterpret_cast<unsigned*>(smem);                     // 2 per local tile
   unsigned* soff = tj + 2 * kEmitMaxTilesPerCta;                        // kEmitStagePairs + 1
   K* skey = reinterpret_cast<K*>(soff + kEmitStagePairs + 2);           // kEmitStagePairs
-  // skey must be 16-byte aligned for K = long long: soff block is (4096+2)*4 B.
   V* vout = reinterpret_cast<V*>(out + head);
 
   for (unsigned long long round = 0;; ++round) {
@@ -805,9 +1165,12 @@ __device__ void phase_emit(const Params& p, unsigned long long npairs, unsigned 
 // ---------------------------------------------------------------------------
 // The persistent pipeline kernel (N >= 2048).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void mark(Ctrl* c, int i) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->rec.timeline[i] = global_timer_ns();
+}
+
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ void pipeline_body(const Params& p, unsigned char* smem) {
   Ctrl* c = p.ctrl;
   const K* keys = reinterpret_cast<const K*>(p.keys);
   K* out = reinterpret_cast<K*>(p.out);
@@ -815,19 +1178,27 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
 
   if ((p.test_flags & kTestSkipBarrier) && blockIdx.x == 0) return;  // test: never arrive
 
+  // The count phase's first chunks are on their way while CTA 0 samples.
+  Ring<K> ring;
+  if (p.mode == kModeSort) ring.start(p, keys, smem);
+  else ring.live = false;
+
   if (blockIdx.x == 0) phase_sample<K>(p, keys, smem);
-  if (!grid_sync(c, epoch, p.timeout_ns)) return;
+  if (!grid_sync(c, epoch, p.timeout_ns)) { ring.drain(p); return; }
+  mark(c, 1);
 
   Record& r = c->rec;
   const int hint = r.sample_nondecreasing;
   if (hint) {
     phase_monotone<K>(p, keys);
-    if (!grid_sync(c, epoch, p.timeout_ns)) return;
+    if (!grid_sync(c, epoch, p.timeout_ns)) { ring.drain(p); return; }
+    mark(c, 2);
     if (ld_relaxed_u32(&c->inversion) == 0u) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         r.dispatch = 1;   // BYPASS_SORTED
         r.path = 1;
       }
+      ring.drain(p);
       if (p.mode == kModeSort && (const void*)keys != (const void*)out) grid_copy<K>(keys, out, p.n);
       return;
     }
@@ -837,26 +1208,30 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
   const int d = r.dispatch;
   unsigned occ = 0;
   if (d == 3 || d == 4) {
-    phase_count<K>(p, keys, smem, d == 3);
+    if (d == 3) phase_count<K, true>(p, keys, smem, ring);
+    else phase_count<K, false>(p, keys, smem, ring);
     if (!grid_sync(c, epoch, p.timeout_ns)) return;
+    mark(c, 3);
     occ = ld_relaxed_u32(&c->occupancy);
     const unsigned long long special = ld_relaxed_u64(&c->special);
-    const unsigned long long miss = ld_relaxed_u64(&c->miss);
     const unsigned long long kp = (unsigned long long)occ + (special ? 1ull : 0ull);
     const bool overflow = ld_relaxed_u32(&c->overflow) != 0u || kp > r.L;
+    // Sec. 4.4: the tiny counters add up to N exactly when every key is one
+    // of the u sampled keys, i.e. when the column has exactly u distinct keys.
     int path;
-    if (d == 3) path = (miss == 0) ? 3 : (overflow ? 8 : 7);
+    if (d == 3) path = (!overflow && kp == (unsigned long long)r.u) ? 3 : (overflow ? 8 : 7);
     else path = overflow ? 6 : 4;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       r.path = path;
       r.k_distinct = overflow ? 0ull : kp;
+      r.n_pairs = overflow ? 0ull : kp;
     }
     if (!overflow) {
-      unsigned long long npairs;
-      if (kp <= (unsigned long long)kSmallPairs) {
-        if (blockIdx.x == 0) phase_small_pairs<K>(p, occ, special, smem);
+      if (occ <= (unsigned)kRankPairs) {
+        phase_rank_pairs<K>(p, occ, special, smem);
         if (!grid_sync(c, epoch, p.timeout_ns)) return;
-        npairs = bit_ceil_u64(kp);
+        mark(c, 4);
+        reset_claimed(p, occ);
       } else {
         // Gather the claimed slots into pair arrays and reset the table.
         K* ak = reinterpret_cast<K*>(p.pkeys_a);
@@ -878,19 +1253,30 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
                                  reinterpret_cast<K*>(p.pkeys_b), p.pvals_b, smem, epoch, 0u))
           return;
         if (!grid_scan_counts(p, p.svals, kp, smem, epoch)) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) r.n_pairs = kp;
-        npairs = kp;
+        mark(c, 4);
       }
-      phase_emit<K>(p, npairs, smem);
+      phase_emit<K>(p, kp, smem);
       return;
     }
     // Guard fired: clear the claimed slots, then fall back to radix.
     reset_claimed(p, occ);
-  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-    r.path = 5;  // HIGH_ENTROPY_RADIX
+  } else {
+    ring.drain(p);
+    if (blockIdx.x == 0 && threadIdx.x == 0) r.path = 5;  // HIGH_ENTROPY_RADIX
   }
   radix_sort<K, false>(p, keys, nullptr, p.n, out, nullptr, reinterpret_cast<K*>(p.tmp), nullptr,
                        smem, epoch, 8u);
+}
+
+// Phase timeline (globaltimer ns): 0 start, 1 sampled, 2 monotone checked,
+// 3 counted, 4 pairs sorted and scanned, 5 last CTA finished.
+template <typename K>
+__global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  mark(p.ctrl, 0);
+  pipeline_body<K>(p, smem);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(&p.ctrl->rec.timeline[5], global_timer_ns());
 }
 
 // ---------------------------------------------------------------------------
@@ -899,14 +1285,14 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
 // ---------------------------------------------------------------------------
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 1) small_kernel(Params p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const K* keys = reinterpret_cast<const K*>(p.keys);
   K* out = reinterpret_cast<K*>(p.out);
   Record& r = p.ctrl->rec;
   phase_sample<K>(p, keys, smem);
   const int n = (int)p.n;
   long long* s = reinterpret_cast<long long*>(smem);
-  for (int i = threadIdx.x; i < 2 * kThreads; i += blockDim.x) s[i] = i < n ? (long long)keys[i] : LLONG_MAX;
+  for (int i = threadIdx.x; i < kSmallCap; i += blockDim.x) s[i] = i < n ? (long long)keys[i] : LLONG_MAX;
   __syncthreads();
   int asc = 1;
   for (int i = threadIdx.x; i + 1 < n; i += blockDim.x) asc &= (s[i] <= s[i + 1]);
@@ -916,7 +1302,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(Params p) {
     r.path = mono ? 1 : 2;
   }
   if (p.mode == kModeEstimate) return;
-  if (!mono) bitonic_sort_pairs(s, nullptr, 2 * kThreads);
+  if (!mono) bitonic_sort_pairs(s, nullptr, kSmallCap);
   if (mono && (const void*)keys == (const void*)out) return;
   for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = (K)s[i];
 }
@@ -930,15 +1316,20 @@ __global__ void fill_u64_kernel(unsigned long long* p, unsigned long long n, uns
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
+// The N < 2048 kernel needs the sampler's FreqSet (4096 x 12 B + samples)
+// and later the column itself (kSmallCap x 8 B).
+constexpr int kSmallSmem = 4096 * 12 + kSamples * 8 + 1024;
+static_assert(kSmallSmem >= kSmallCap * 8, "small-kernel shared memory");
+
 cudaError_t prepare_kernels() {
   cudaError_t e;
   e = cudaFuncSetAttribute(pipeline_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipelineSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pipeline_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipelineSmem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(small_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kThreads * 8 + 256);
+  e = cudaFuncSetAttribute(small_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(small_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kThreads * 8 + 256);
+  return cudaFuncSetAttribute(small_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmem);
 }
 
 cudaError_t pipeline_occupancy(int dtype, int* blocks_per_sm) {
@@ -956,9 +1347,8 @@ cudaError_t launch_pipeline(const Params& p, int dtype, int grid, cudaStream_t s
 }
 
 cudaError_t launch_small(const Params& p, int dtype, cudaStream_t s) {
-  const int smem = 2 * kThreads * 8 + 256;
-  if (dtype == 0) small_kernel<int><<<1, kThreads, smem, s>>>(p);
-  else small_kernel<long long><<<1, kThreads, smem, s>>>(p);
+  if (dtype == 0) small_kernel<int><<<1, kThreads, kSmallSmem, s>>>(p);
+  else small_kernel<long long><<<1, kThreads, kSmallSmem, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -56,31 +56,33 @@ def _unit_float(r: np.ndarray) -> np.ndarray:
     return (r >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
 
 
-def distinct_values(k: int, seed: int, dtype=np.int64, exclude=None) -> np.ndarray:
-    """K distinct values uniform over the dtype's full range (rejection)."""
-    info = np.iinfo(dtype)
-    out = np.empty(0, dtype=dtype)
-    draw = 0
-    excl = None if exclude is None else np.asarray(exclude, dtype=dtype)
-    while out.size < k:
-        need = k - out.size
-        batch = max(16, int(need * 1.1) + 16)
-        r = splitmix64(seed, batch, offset=draw)
-        draw += batch
-        if dtype == np.int64:
-            v = r.view(np.int64)
-        else:
-            v = (r >> np.uint64(32)).astype(np.uint32).view(np.int32)
-        v = v.astype(dtype, copy=False)
-        cand = np.concatenate([out, v])
-        _, first = np.unique(cand, return_index=True)
-        keep = np.zeros(cand.size, dtype=bool)
-        keep[np.sort(first)] = True
-        if excl is not None and excl.size:
-            keep &= ~np.isin(cand, excl)
-        out = cand[keep][:k]
-        assert out.min() >= info.min and out.max() <= info.max
-    return out
+def _mix32(x: np.ndarray) -> np.ndarray:
+    """A bijection on 32-bit words (xorshift-multiply finaliser, 'lowbias32')."""
+    x = x.astype(np.uint32, copy=True)
+    with np.errstate(over="ignore"):
+        x ^= x >> np.uint32(16)
+        x *= np.uint32(0x7FEB352D)
+        x ^= x >> np.uint32(15)
+        x *= np.uint32(0x846CA68B)
+        x ^= x >> np.uint32(16)
+    return x
+
+
+def distinct_values(k: int, seed: int, dtype=np.int64, start: int = 0) -> np.ndarray:
+    """K distinct values spread over the dtype's full range, in random order.
+
+    Draws ``start .. start+k-1`` of a bijective counter mix: SplitMix64 for
+    64-bit keys (its counter step is odd and its finaliser is a bijection, so
+    distinct counters give distinct values) and a 32-bit bijective mix of
+    ``seed + counter`` for 32-bit keys.  Two calls with the same seed and
+    disjoint ``start`` ranges therefore never share a value.
+    """
+    if dtype == np.int64:
+        return splitmix64(seed, k, offset=start).view(np.int64)
+    if k + start > (1 << 32):
+        raise ValueError("at most 2^32 distinct 32-bit values")
+    ctr = (np.arange(start, start + k, dtype=np.uint64) + np.uint64(seed & 0xFFFFFFFF)) & np.uint64(0xFFFFFFFF)
+    return _mix32(ctr).view(np.int32)
 
 
 def shuffle(values: np.ndarray, seed: int) -> np.ndarray:
@@ -117,9 +119,8 @@ def column(n: int, k: int, dist: str = "uniform", dtype=np.int64, seed: int = 0,
     """
     base = 42 + n + k
     if k >= n:
-        return shuffle(distinct_values(n, base ^ seed, dtype), base + seed)
+        return distinct_values(n, base ^ seed, dtype)
     pal = distinct_values(k, base ^ seed, dtype)
-    pal = shuffle(pal, base + 7 * seed + 1)
     if dist == "uniform":
         ranks = uniform_ranks(n, k, base * 31 + seed)
     elif dist == "zipf":
@@ -159,7 +160,7 @@ def spill_trigger(n: int, dtype=np.int64, seed: int = 0, small_set: int = 64) ->
     small = distinct_values(small_set, 1000 + seed, dtype)
     reps = -(-npos // small_set)
     sample_vals = shuffle(np.tile(small, reps)[:npos], 2000 + seed)
-    rest = distinct_values(n - npos, 3000 + seed, dtype, exclude=small)
+    rest = distinct_values(n - npos, 1000 + seed, dtype, start=small_set)
     out = np.empty(n, dtype=dtype)
     mask = np.ones(n, dtype=bool)
     mask[pos] = False

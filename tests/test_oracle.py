@@ -182,7 +182,7 @@ def _guard_column(k_true, seed=0):
     x = np.empty(n, np.int64)
     pos = np.arange(1024) * 8
     x[pos] = G.shuffle(np.tile(small, 64), 12 + seed)
-    extra = G.distinct_values(k_true - 16, 13 + seed, np.int64, exclude=small)
+    extra = G.distinct_values(k_true - 16, 11 + seed, np.int64, start=16)
     rest = np.concatenate([extra, np.resize(small, n - 1024 - extra.size)])
     mask = np.ones(n, bool)
     mask[pos] = False
