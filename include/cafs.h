@@ -140,6 +140,22 @@ cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype,
 cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype,
                            void* host_out, cafs_report* report, void* stream);
 
+/* Allocation-free variant of cafs_sort (the paper has no counterpart).  For
+ * callers that cannot allocate device memory -- code inside a CUDA graph
+ * capture that must not add allocation nodes, engines that allow no memory
+ * outside pre-reserved pools, locked-down allocators: this call performs no
+ * cudaMalloc/cudaFree and calls no allocating library routine.  Its scratch
+ * is one file-scope device array of about 22 MiB that every GPU loading the
+ * library holds until the process exits.  n must be <= 2^19 (524288) keys,
+ * else CAFS_ERR_TOO_LARGE; other arguments as for cafs_sort.  The first call
+ * on a device resolves the array's device address and sets kernel
+ * attributes, so make that first call before any stream capture.  All calls
+ * share the array (it keeps the previous call's contents and is re-cleared
+ * per call): calls whose work overlaps on the GPU -- other streams, other
+ * host threads -- race and must be serialised by the caller.  No report. */
+cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype dtype, void* out,
+                              void* stream);
+
 /* Testing hooks (no counterpart in the paper).  `flags` bit 0 makes CTA 0 of
  * the next pipeline launches skip the first grid barrier, so that the other
  * CTAs' bounded wait runs out and the launch reports CAFS_ERR_TIMEOUT in

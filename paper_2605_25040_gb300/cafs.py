@@ -70,6 +70,8 @@ SIGNATURES = {
                                        ctypes.POINTER(Estimate), ctypes.c_void_p]),
     "cafs_sort_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                       ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
+    "cafs_sort_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "cafs_set_test_hooks": (None, [ctypes.c_uint32, ctypes.c_uint64]),
     "cafs_kernel_launch_count": (ctypes.c_uint64, []),
     "cafs_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -54,26 +54,6 @@ struct Workspace {
 };
 std::map<std::pair<int, uintptr_t>, Workspace*> g_ws;
 
-unsigned long long bit_ceil_host(unsigned long long x) {
-  unsigned long long r = 1;
-  while (r < x) r <<= 1;
-  return r;
-}
-
-// Largest Chao1 estimate short of saturation: u = 1022 distinct samples, 1021
-// of them seen once and one seen three times (Eq. 5 maximised over the sample
-// spectra with u < 1024).  Any main-path table is sized from K_hat <= this.
-constexpr unsigned long long kMaxUnsaturatedKhat = 522242ull;
-
-unsigned long long table_capacity(unsigned long long n, int dtype) {
-  const unsigned long long cap = dtype == CAFS_INT64 ? 4 : 8;
-  unsigned long long m = bit_ceil_host((8ull * kMaxUnsaturatedKhat) / cap);
-  const unsigned long long upper = bit_ceil_host((n + cap - 1) / cap);
-  if (m > upper) m = upper;
-  if (m < 8) m = 8;
-  return m * cap;
-}
-
 template <typename T>
 void free_dev(T*& p) {
   if (p) cudaFree((void*)p);
@@ -116,10 +96,8 @@ cafs_status ensure_workspace(Workspace* w, unsigned long long n, int dtype, cuda
                              bool need_io) {
   const size_t kb = dtype == CAFS_INT64 ? 8 : 4;
   const unsigned long long tcap = table_capacity(n, dtype);
-  unsigned long long pcap = tcap / 2 + 2;
-  if (pcap < (unsigned long long)kSmallPairs) pcap = kSmallPairs;
-  const unsigned long long items = n > pcap ? n : pcap;
-  const unsigned long long lcap = ((items + kRadixTile - 1) / kRadixTile) * kRadixDigits;
+  const unsigned long long pcap = pair_capacity(tcap);
+  const unsigned long long lcap = lookback_words(n > pcap ? n : pcap);
   const size_t tmp_bytes = (size_t)n * kb;
   const bool grow = !w->ctrl || tcap > w->table_cap || pcap > w->pair_cap ||
                     lcap > w->lookback_cap || tmp_bytes > w->tmp_bytes;

@@ -138,6 +138,41 @@ struct Params {
   unsigned long long timeout_ns;
 };
 
+// ---------------------------------------------------------------------------
+// Workspace sizing shared by the host entry points.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long bit_ceil_host(unsigned long long x) {
+  unsigned long long r = 1;
+  while (r < x) r <<= 1;
+  return r;
+}
+
+// Largest Chao1 estimate short of saturation: u = 1022 distinct samples, 1021
+// of them seen once and one seen three times (Eq. 5 maximised over the sample
+// spectra with u < 1024).  Any main-path table is sized from K_hat <= this.
+constexpr unsigned long long kMaxUnsaturatedKhat = 522242ull;
+
+// Slots of the largest global table a column of n keys can need (Eq. 6 with
+// K_hat <= kMaxUnsaturatedKhat and the clamps).  dtype 1 = int64, 0 = int32.
+constexpr unsigned long long table_capacity(unsigned long long n, int dtype) {
+  const unsigned long long cap = dtype == 1 ? 4 : 8;
+  unsigned long long m = bit_ceil_host((8ull * kMaxUnsaturatedKhat) / cap);
+  const unsigned long long upper = bit_ceil_host((n + cap - 1) / cap);
+  if (m > upper) m = upper;
+  if (m < 8) m = 8;
+  return m * cap;
+}
+
+// Entries of the pair arrays for a table of tcap slots (L + the type minimum).
+constexpr unsigned long long pair_capacity(unsigned long long tcap) {
+  return tcap / 2 + 2 > (unsigned long long)kSmallPairs ? tcap / 2 + 2 : (unsigned long long)kSmallPairs;
+}
+
+// Look-back words for radix sorts of up to `items` items.
+constexpr unsigned long long lookback_words(unsigned long long items) {
+  return ((items + kRadixTile - 1) / kRadixTile) * kRadixDigits;
+}
+
 // Host-side launchers (defined in cafs_pipeline.cu).
 cudaError_t launch_pipeline(const Params& p, int dtype, int grid, cudaStream_t s);
 cudaError_t launch_small(const Params& p, int dtype, cudaStream_t s);
