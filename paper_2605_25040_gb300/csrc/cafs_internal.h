@@ -21,6 +21,8 @@ constexpr int kTinyBuckets = 1 << kTinyBucketBits;
 
 // Threads per CTA of every kernel in the library (one CTA per SM).
 constexpr int kThreads = 1024;
+// Largest grid of the persistent pipeline (per-CTA arrays are sized by it).
+constexpr int kMaxGrid = 1024;
 constexpr int kWarps = kThreads / 32;
 
 // Dynamic shared memory of the persistent pipeline kernel (bytes): during
@@ -106,7 +108,7 @@ struct Ctrl {
   unsigned pad2;
   unsigned long long special;   // keys equal to the type minimum (the empty marker)
   unsigned long long unused0;
-  unsigned tickets[16];         // radix: per-pass tile tickets
+  unsigned unused_tickets[16];
   unsigned hist[8][kRadixDigits];  // radix: global digit counts per pass
   unsigned long long chunk_sums[1024];  // scan: per-CTA partial sums
 };
@@ -129,7 +131,7 @@ struct Params {
   unsigned long long pair_cap;
   // radix fallback temp buffer (n keys) and look-back status words
   void* tmp;
-  unsigned long long* lookback;
+  unsigned long long* lookback;       // radix scratch: per-CTA digit counts and bases
   unsigned long long lookback_cap;   // words
   long long* sample_keys;            // kSamples: distinct sampled keys, ascending
   unsigned gen;          // call generation (tags look-back words)
@@ -168,9 +170,10 @@ constexpr unsigned long long pair_capacity(unsigned long long tcap) {
   return tcap / 2 + 2 > (unsigned long long)kSmallPairs ? tcap / 2 + 2 : (unsigned long long)kSmallPairs;
 }
 
-// Look-back words for radix sorts of up to `items` items.
-constexpr unsigned long long lookback_words(unsigned long long items) {
-  return ((items + kRadixTile - 1) / kRadixTile) * kRadixDigits;
+// 64-bit words of the radix scratch: per-CTA digit counts and bases, two
+// [kMaxGrid][kRadixDigits] arrays of 32-bit words (independent of n).
+constexpr unsigned long long lookback_words(unsigned long long /*items*/) {
+  return (unsigned long long)kMaxGrid * kRadixDigits;
 }
 
 // Host-side launchers (defined in cafs_pipeline.cu).

@@ -22,13 +22,14 @@
 //   4  emit: every output tile looks up its runs and writes them with 16-byte
 //      streaming stores (the paper's fill_n per pair)
 //   R  radix fallback (the paper's pdqsort: 2*K_hat > N, or the guard fired):
-//      LSD radix sort, 8-bit digits, one-sweep passes with decoupled
-//      look-back; passes whose digit is constant are skipped.
+//      LSD radix sort, 8-bit digits; one histogram read for all passes, then
+//      per pass a reduce-then-scan over per-CTA digit counts and an in-order
+//      stable scatter; passes whose digit is constant are skipped.
 //
 // Columns with N < 2048 are sorted by a single CTA in shared memory
 // (Table 2: "sampling does not amortize").
 //
-// All device waits (grid barrier, mbarriers, look-back) are bounded by a
+// All device waits (grid barrier, mbarriers) are bounded by a
 // timeout; a wait that runs out records kDevTimeout and the launch ends early
 // after draining its own bulk copies.
 
@@ -402,7 +403,7 @@ __device__ __noinline__ void global_insert(GlobalTable g, unsigned long long key
   const unsigned long long h = hash_slot(key64, g.logC);
   for (unsigned long long probe = 0; probe < g.C; ++probe) {
     // Once the guard has fired the counts are discarded: stop probing.
-    if ((probe & 15ull) == 15ull && ld_relaxed_u32(&c->overflow)) return;
+    if ((probe & 3ull) == 3ull && ld_relaxed_u32(&c->overflow)) return;
     const unsigned long long slot = (h + probe) & mask;
     const unsigned long long k = ld_relaxed_u64(g.keys + slot);
     if (k == key64) {
@@ -804,78 +805,141 @@ __device__ __forceinline__ unsigned radix_digit(K k, int shift) {
   return (unsigned)(u >> shift) & (kRadixDigits - 1);
 }
 
-constexpr unsigned long long kFlagAgg = 1ull, kFlagIncl = 2ull;
-
+// One stable counting pass on digit `pass` (8 bits at 8*pass), all CTAs.
+// CTA b owns the contiguous tiles [b*T/G, (b+1)*T/G) and scatters them in
+// order, so each digit's output position is
+//   dstart[d] + (keys with digit d in CTAs before b) + (earlier tiles of b)
+//   + (rank within the tile).
+// (a) every CTA counts digit d over its range; (b) the CTAs scan those
+// counts (CTA b takes digits d = b, b + G, ...), with a grid barrier after
+// each step; (c) every CTA ranks each tile in shared memory (stable: a
+// per-warp match on the digit, warps in order) and writes it out.
 template <typename K, bool PAY>
-__device__ void radix_pass(const Params& p, const K* in_k, const unsigned* in_v, K* out_k,
-                           unsigned* out_v, unsigned long long n, int pass, unsigned tag,
-                           unsigned char* smem) {
+__device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v, K* out_k,
+                           unsigned* out_v, unsigned long long n, int pass, unsigned char* smem,
+                           unsigned& epoch) {
   Ctrl* c = p.ctrl;
   const int shift = pass * kRadixBits;
   const unsigned long long ntiles = (n + kRadixTile - 1) / kRadixTile;
+  const unsigned b = blockIdx.x, nb = gridDim.x;
+  const unsigned long long tile0 = ntiles * b / nb, tile1 = ntiles * (b + 1) / nb;
+  unsigned* cta_cnt = reinterpret_cast<unsigned*>(p.lookback);       // [nb][256]
+  unsigned* cta_base = cta_cnt + kMaxGrid * kRadixDigits;             // [nb][256]
+
   K* stage_k = reinterpret_cast<K*>(smem);
   unsigned* stage_v = reinterpret_cast<unsigned*>(stage_k + kRadixTile);
   unsigned short* wcnt = reinterpret_cast<unsigned short*>(stage_v + (PAY ? kRadixTile : 0));
   unsigned* tile_cnt = reinterpret_cast<unsigned*>(wcnt + kWarps * kRadixDigits);
   unsigned* tile_start = tile_cnt + kRadixDigits;
-  unsigned* gbase = tile_start + kRadixDigits;
-  unsigned* dstart = gbase + kRadixDigits;
-  unsigned* scratch = dstart + kRadixDigits;  // kWarps
-  unsigned* s_ticket = scratch + kWarps;
+  unsigned* running = tile_start + kRadixDigits;
+  unsigned* hist = running + kRadixDigits;
+  unsigned* scratch = hist + kRadixDigits;    // kWarps
+  unsigned* scan_part = scratch + kWarps;     // kThreads
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned long long tagbits = ((unsigned long long)(tag & 0x3FFFFFFFu)) << 34;
 
-  // Global exclusive start of every digit for this pass.
+  // (a) digit counts of this CTA's range
+  if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = 0u;
+  __syncthreads();
+  {
+    const unsigned long long i0 = tile0 * kRadixTile;
+    const unsigned long long i1 = tile1 * kRadixTile < n ? tile1 * kRadixTile : n;
+    constexpr int U = 4;
+    for (unsigned long long base = i0 + threadIdx.x; base < i1; base += (unsigned long long)U * kThreads) {
+      K kk[U];
+      #pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const unsigned long long i = base + (unsigned long long)j * kThreads;
+        kk[j] = i < i1 ? __ldcg(in_k + i) : (K)0;
+      }
+      #pragma unroll
+      for (int j = 0; j < U; ++j)
+        if (base + (unsigned long long)j * kThreads < i1) atomicAdd(hist + radix_digit(kk[j], shift), 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kRadixDigits) cta_cnt[b * kRadixDigits + threadIdx.x] = hist[threadIdx.x];
+  if (!grid_sync(c, epoch, p.timeout_ns)) return false;
+
+  // (b) exclusive scan over CTAs of each digit (this CTA's digits), offset
+  // by the digit's global start (exclusive scan of the pass histogram)
   {
     const unsigned v = threadIdx.x < kRadixDigits ? ld_relaxed_u32(&c->hist[pass][threadIdx.x]) : 0u;
     unsigned tot;
     const unsigned ex = block_exclusive_scan(v, scratch, &tot);
-    if (threadIdx.x < kRadixDigits) dstart[threadIdx.x] = ex;
+    if (threadIdx.x < kRadixDigits) tile_start[threadIdx.x] = ex;   // digit starts (reused below)
   }
-  for (;;) {
+  __syncthreads();
+  for (int d = (int)b; d < kRadixDigits; d += (int)nb) {
+    const unsigned dstart = tile_start[d];
+    const unsigned v = threadIdx.x < nb ? __ldcg(cta_cnt + threadIdx.x * kRadixDigits + d) : 0u;
+    unsigned tot;
+    const unsigned ex = block_exclusive_scan(v, scratch, &tot);
+    if (threadIdx.x < nb) cta_base[threadIdx.x * kRadixDigits + d] = dstart + ex;
+  }
+  if (!grid_sync(c, epoch, p.timeout_ns)) return false;
+
+  // (c) rank and scatter this CTA's tiles in order
+  if (threadIdx.x < kRadixDigits) running[threadIdx.x] = __ldcg(cta_base + b * kRadixDigits + threadIdx.x);
+  for (unsigned long long tile = tile0; tile < tile1; ++tile) {
     __syncthreads();
-    if (threadIdx.x == 0) *s_ticket = atomicAdd(&c->tickets[pass], 1u);
-    __syncthreads();
-    const unsigned long long tile = *s_ticket;
-    if (tile >= ntiles) break;
     const unsigned long long base = tile * kRadixTile;
     for (int d = lane; d < kRadixDigits; d += 32) wcnt[w * kRadixDigits + d] = 0;
     __syncwarp();
     K key[kRadixItems];
-    unsigned val[kRadixItems];
-    unsigned short rank[kRadixItems];
-    unsigned dig[kRadixItems];
+    unsigned rd[kRadixItems];   // rank within the warp << 16 | digit (256 = no item)
+    const unsigned long long wbase = base + (unsigned long long)w * (32 * kRadixItems) + lane;
     #pragma unroll
     for (int j = 0; j < kRadixItems; ++j) {
-      const unsigned long long idx = base + (unsigned long long)w * (32 * kRadixItems) + j * 32 + lane;
+      const unsigned long long idx = wbase + j * 32;
       const bool valid = idx < n;
       key[j] = valid ? __ldcg(in_k + idx) : (K)0;
-      if constexpr (PAY) val[j] = valid ? __ldcg(in_v + idx) : 0u;
-      dig[j] = valid ? radix_digit(key[j], shift) : (unsigned)kRadixDigits;
+      rd[j] = valid ? radix_digit(key[j], shift) : (unsigned)kRadixDigits;
     }
     #pragma unroll
     for (int j = 0; j < kRadixItems; ++j) {
-      const unsigned d = dig[j];
+      const unsigned d = rd[j];
       const unsigned peers = __match_any_sync(0xffffffffu, d);
-      unsigned old = 0;
-      if (d < (unsigned)kRadixDigits) old = wcnt[w * kRadixDigits + d];
-      __syncwarp();
       const int leader = __ffs(peers) - 1;
-      if (lane == leader && d < (unsigned)kRadixDigits)
+      unsigned old = 0;
+      if (lane == leader && d < (unsigned)kRadixDigits) {
+        old = wcnt[w * kRadixDigits + d];
         wcnt[w * kRadixDigits + d] = (unsigned short)(old + __popc(peers));
+      }
+      old = __shfl_sync(0xffffffffu, old, leader);
       __syncwarp();
-      rank[j] = (unsigned short)(old + __popc(peers & lanemask_lt()));
+      rd[j] = d | ((old + __popc(peers & lanemask_lt())) << 16);
     }
     __syncthreads();
-    // Per digit: exclusive scan over warps, tile total.
-    if (threadIdx.x < kRadixDigits) {
+    // Per digit: exclusive scan over warps and tile total.  kScanGroups
+    // threads per digit each scan a slice of the warps, then the slices'
+    // totals are combined.
+    {
+      constexpr int kScanGroups = kThreads / kRadixDigits;
+      constexpr int kWarpsPerGroup = kWarps / kScanGroups;
+      static_assert(kScanGroups * kRadixDigits == kThreads, "scan groups");
+      const int d = threadIdx.x % kRadixDigits, g = threadIdx.x / kRadixDigits;
       unsigned run = 0;
-      for (int q = 0; q < kWarps; ++q) {
-        const unsigned x = wcnt[q * kRadixDigits + threadIdx.x];
-        wcnt[q * kRadixDigits + threadIdx.x] = (unsigned short)run;
+      #pragma unroll
+      for (int q = g * kWarpsPerGroup; q < (g + 1) * kWarpsPerGroup; ++q) {
+        const unsigned x = wcnt[q * kRadixDigits + d];
+        wcnt[q * kRadixDigits + d] = (unsigned short)run;
         run += x;
       }
-      tile_cnt[threadIdx.x] = run;
+      scan_part[g * kRadixDigits + d] = run;
+      __syncthreads();
+      unsigned before = 0, tot = 0;
+      #pragma unroll
+      for (int q = 0; q < kScanGroups; ++q) {
+        const unsigned v = scan_part[q * kRadixDigits + d];
+        before += q < g ? v : 0u;
+        tot += v;
+      }
+      if (g > 0) {
+        #pragma unroll
+        for (int q = g * kWarpsPerGroup; q < (g + 1) * kWarpsPerGroup; ++q)
+          wcnt[q * kRadixDigits + d] = (unsigned short)(wcnt[q * kRadixDigits + d] + before);
+      }
+      if (g == 0) tile_cnt[d] = tot;
     }
     __syncthreads();
     {
@@ -884,58 +948,31 @@ __device__ void radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
       const unsigned ex = block_exclusive_scan(v, scratch, &tot);
       if (threadIdx.x < kRadixDigits) tile_start[threadIdx.x] = ex;
     }
-    // Decoupled look-back: digit d's exclusive prefix over earlier tiles.
-    if (threadIdx.x < kRadixDigits) {
-      const int d = threadIdx.x;
-      unsigned long long* st = p.lookback + tile * kRadixDigits + d;
-      const unsigned agg = tile_cnt[d];
-      unsigned excl = 0;
-      if (tile == 0) {
-        st_release_u64(st, tagbits | (kFlagIncl << 32) | agg);
-      } else {
-        st_release_u64(st, tagbits | (kFlagAgg << 32) | agg);
-        long long look = (long long)tile - 1;
-        const unsigned long long t0 = global_timer_ns();
-        unsigned it = 0;
-        while (look >= 0) {
-          const unsigned long long wv = ld_acquire_u64(p.lookback + (unsigned long long)look * kRadixDigits + d);
-          const unsigned long long flag = (wv >> 32) & 3ull;
-          if ((wv & ~((1ull << 34) - 1)) != tagbits || flag == 0) {
-            if ((++it & 63u) == 0 && global_timer_ns() - t0 > p.timeout_ns) {
-              atomicExch(&c->rec.status, kDevTimeout);
-              break;
-            }
-            continue;
-          }
-          excl += (unsigned)(wv & 0xFFFFFFFFull);
-          if (flag == kFlagIncl) break;
-          --look;
-        }
-        st_release_u64(st, tagbits | (kFlagIncl << 32) | (unsigned long long)(excl + agg));
-      }
-      gbase[d] = dstart[d] + excl - tile_start[d];
-    }
     __syncthreads();
     // Scatter into shared memory in tile-sorted order.
     #pragma unroll
     for (int j = 0; j < kRadixItems; ++j) {
-      const unsigned d = dig[j];
+      const unsigned d = rd[j] & 0xFFFFu;
       if (d < (unsigned)kRadixDigits) {
-        const unsigned pos = tile_start[d] + wcnt[w * kRadixDigits + d] + rank[j];
+        const unsigned pos = tile_start[d] + wcnt[w * kRadixDigits + d] + (rd[j] >> 16);
         stage_k[pos] = key[j];
-        if constexpr (PAY) stage_v[pos] = val[j];
+        if constexpr (PAY) stage_v[pos] = __ldcg(in_v + wbase + j * 32);
       }
     }
     __syncthreads();
     const unsigned cnt = (unsigned)((n - base) < (unsigned long long)kRadixTile ? (n - base) : kRadixTile);
     for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) {
       const K k = stage_k[i];
-      const unsigned long long dst = (unsigned long long)(unsigned)(gbase[radix_digit(k, shift)] + i);
+      const unsigned d = radix_digit(k, shift);
+      const unsigned long long dst = (unsigned long long)(unsigned)(running[d] + (i - tile_start[d]));
       __stcg(out_k + dst, k);
       if constexpr (PAY) __stcg(out_v + dst, stage_v[i]);
     }
+    __syncthreads();
+    if (threadIdx.x < kRadixDigits) running[threadIdx.x] += tile_cnt[threadIdx.x];
   }
   __syncthreads();
+  return true;
 }
 
 // Full LSD radix sort src -> dst (tmp as ping-pong), all CTAs.  Returns false
@@ -943,22 +980,33 @@ __device__ void radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
 template <typename K, bool PAY>
 __device__ bool radix_sort(const Params& p, const K* src_k, const unsigned* src_v,
                            unsigned long long n, K* dst_k, unsigned* dst_v, K* tmp_k,
-                           unsigned* tmp_v, unsigned char* smem, unsigned& epoch,
-                           unsigned tag_base) {
+                           unsigned* tmp_v, unsigned char* smem, unsigned& epoch) {
   using T = KeyTraits<K>;
   constexpr int NP = T::kPasses;
   Ctrl* c = p.ctrl;
-  // Histogram of every digit of every pass.
+  // Histogram of every digit of every pass (one read of the keys).
   unsigned* sh = reinterpret_cast<unsigned*>(smem);
   for (int i = threadIdx.x; i < NP * kRadixDigits; i += blockDim.x) sh[i] = 0u;
   __syncthreads();
   {
     const unsigned long long G = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (unsigned long long i = gt; i < n; i += G) {
-      const typename T::U u = (typename T::U)__ldcg(src_k + i) ^ T::kSign;
+    constexpr int U = 4;
+    for (unsigned long long base = gt; base < n; base += G * U) {
+      K kk[U];
       #pragma unroll
-      for (int q = 0; q < NP; ++q) atomicAdd(sh + q * kRadixDigits + ((u >> (q * kRadixBits)) & 0xFF), 1u);
+      for (int j = 0; j < U; ++j) {
+        const unsigned long long i = base + (unsigned long long)j * G;
+        kk[j] = i < n ? __ldcg(src_k + i) : (K)0;
+      }
+      #pragma unroll
+      for (int j = 0; j < U; ++j) {
+        if (base + (unsigned long long)j * G < n) {
+          const typename T::U u = (typename T::U)kk[j] ^ T::kSign;
+          #pragma unroll
+          for (int q = 0; q < NP; ++q) atomicAdd(sh + q * kRadixDigits + ((u >> (q * kRadixBits)) & 0xFF), 1u);
+        }
+      }
     }
   }
   __syncthreads();
@@ -1002,8 +1050,7 @@ __device__ bool radix_sort(const Params& p, const K* src_k, const unsigned* src_
     K* ok_ = to_dst ? dst_k : tmp_k;
     unsigned* ov = to_dst ? dst_v : tmp_v;
     const int pass = (int)((active_bits >> (4 * a)) & 15u);
-    const unsigned tag = (p.gen << 4) | ((tag_base + (unsigned)pass) & 15u);
-    radix_pass<K, PAY>(p, cur_k, cur_v, ok_, ov, n, pass, tag, smem);
+    if (!radix_pass<K, PAY>(p, cur_k, cur_v, ok_, ov, n, pass, smem, epoch)) return false;
     if (!grid_sync(c, epoch, p.timeout_ns)) return false;
     cur_k = ok_;
     cur_v = ov;
@@ -1250,7 +1297,7 @@ __device__ void pipeline_body(const Params& p, unsigned char* smem) {
         }
         if (!grid_sync(c, epoch, p.timeout_ns)) return;
         if (!radix_sort<K, true>(p, ak, p.pvals_a, kp, reinterpret_cast<K*>(p.skeys), p.svals,
-                                 reinterpret_cast<K*>(p.pkeys_b), p.pvals_b, smem, epoch, 0u))
+                                 reinterpret_cast<K*>(p.pkeys_b), p.pvals_b, smem, epoch))
           return;
         if (!grid_scan_counts(p, p.svals, kp, smem, epoch)) return;
         mark(c, 4);
@@ -1265,7 +1312,7 @@ __device__ void pipeline_body(const Params& p, unsigned char* smem) {
     if (blockIdx.x == 0 && threadIdx.x == 0) r.path = 5;  // HIGH_ENTROPY_RADIX
   }
   radix_sort<K, false>(p, keys, nullptr, p.n, out, nullptr, reinterpret_cast<K*>(p.tmp), nullptr,
-                       smem, epoch, 8u);
+                       smem, epoch);
 }
 
 // Phase timeline (globaltimer ns): 0 start, 1 sampled, 2 monotone checked,
