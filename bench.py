@@ -186,6 +186,8 @@ def main():
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--columns", default="",
+                    help="comma-separated subset of sweep columns (e.g. uniform_K200); default all")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -210,7 +212,13 @@ def main():
 
     n = args.n
     specs = sweep_specs(n)
-    host_cols = [(s["name"], make_column(s, n, seed=i)) for i, s in enumerate(specs)]
+    seeds = {s["name"]: i for i, s in enumerate(specs)}
+    if args.columns:
+        keep = set(args.columns.split(","))
+        specs = [s for s in specs if s["name"] in keep]
+        if not specs:
+            raise SystemExit(f"no sweep column matches {args.columns}")
+    host_cols = [(s["name"], make_column(s, n, seed=seeds[s["name"]])) for s in specs]
     dev_in = [torch.from_numpy(x).cuda() for _, x in host_cols]
     dev_out = [torch.empty_like(t) for t in dev_in]
     stream = torch.cuda.current_stream()
@@ -263,7 +271,8 @@ def main():
     bytes_per_col = 2 * 8 * n
     achieved = bytes_per_col * ncol / (sum(col_ms) / 1e3) / 1e9
     main_idx = [i for i, s in enumerate(specs) if s["K"] is not None and s["K"] <= 100_000]
-    main_ach = bytes_per_col * len(main_idx) / (sum(col_ms[i] for i in main_idx) / 1e3) / 1e9
+    main_ms = sum(col_ms[i] for i in main_idx)
+    main_ach = bytes_per_col * len(main_idx) / (main_ms / 1e3) / 1e9 if main_idx else 0.0
 
     # branch taken per column + verification against torch.sort on the device
     sweep = []
@@ -274,8 +283,15 @@ def main():
             ref = torch.sort(dev_in[i]).values
             ok = bool(torch.equal(ref, out))
             verified &= ok
+        tl = rep["timeline_ns"]
+        phases = {}
+        prev = tl[0]
+        for idx, nm in ((1, "sample"), (2, "monotone"), (3, "count"), (4, "pairs"), (5, "finish")):
+            if tl[idx]:
+                phases[nm] = round((tl[idx] - prev) / 1e3, 1)
+                prev = tl[idx]
         sweep.append({"column": name, "path": cafs.path_name(rep["path"]), "k_hat": rep["est"]["k_hat"],
-                      "k_distinct": rep["k_distinct"], "ms": round(col_ms[i], 4),
+                      "k_distinct": rep["k_distinct"], "ms": round(col_ms[i], 4), "phases_us": phases,
                       "gkeys_s": round(n / (col_ms[i] / 1e3) / 1e9, 2),
                       "frac_hbm": round(bytes_per_col / (col_ms[i] / 1e3) / 1e9 / peak, 4)})
 
@@ -298,11 +314,12 @@ def main():
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi,
                "api": "cafs_sort_host (pinned host buffers, blocking per column)"}
         if not args.no_verify:
-            verified &= bool(np.array_equal(pin_out[3].numpy(), np.sort(host_cols[3][1])))
+            verified &= bool(np.array_equal(pin_out[0].numpy(), np.sort(host_cols[0][1])))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline([host_cols[i] for i in (3, 13, 4, 0)])
+        pick = [c for c in host_cols if c[0] in ("uniform_K200", "zipf_K4096", "uniform_K4096", "uniform_K4")]
+        cpu = cpu_baseline(pick or host_cols[:2])
 
     line = {
         "metric": METRIC,

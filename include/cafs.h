@@ -145,7 +145,7 @@ cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype,
  * capture that must not add allocation nodes, engines that allow no memory
  * outside pre-reserved pools, locked-down allocators: this call performs no
  * cudaMalloc/cudaFree and calls no allocating library routine.  Its scratch
- * is one file-scope device array of about 22 MiB that every GPU loading the
+ * is one file-scope device array of about 24 MiB that every GPU loading the
  * library holds until the process exits.  n must be <= 2^19 (524288) keys,
  * else CAFS_ERR_TOO_LARGE; other arguments as for cafs_sort.  The first call
  * on a device resolves the array's device address and sets kernel
@@ -155,6 +155,70 @@ cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype,
  * host threads -- race and must be serialised by the caller.  No report. */
 cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype dtype, void* out,
                               void* stream);
+
+/* ---- Batched form (no counterpart in the paper) -----------------------------
+ * Many columns sorted by one persistent cooperative launch, one CTA per SM.
+ * Each column gets exactly the result, path and report that cafs_sort_ex
+ * gives it alone.  Columns with n >= grid_min_n are sorted one after another
+ * by all CTAs together; the others form a work queue, longest first, from
+ * which each CTA takes whole columns and sorts each alone; radix-fallback
+ * columns of the queue with n >= defer_min_n are set aside and sorted by all
+ * CTAs at the end.  Columns are independent: no two columns of a batch may
+ * overlap in memory (keys == out within one column is allowed). */
+typedef struct {
+  const void* keys;    /* device pointer, n elements                        */
+  void* out;           /* device pointer, n elements; may equal keys        */
+  size_t n;
+  cafs_dtype dtype;
+  int32_t reserved;    /* must be 0                                          */
+} cafs_column;
+
+/* Scheduling knobs of the batched kernel.  They change the speed, never a
+ * result.  0 in any field selects the default (cafs_batch_tuning_default). */
+typedef struct {
+  uint64_t grid_min_n;      /* all-CTA columns: n >= this (>= 2048; 2^21)  */
+  uint64_t defer_min_n;     /* set-aside radix columns: n >= this (2^15)    */
+  uint32_t local_slots_max; /* per-CTA shared hash table cap, slots: power
+                               of two in [256, 8192] (8192)                */
+  uint32_t replicas_max;    /* counter replicas per shared slot: power of
+                               two in [1, 32] (32)                         */
+  uint32_t emit_tile_vec;   /* emit tile in 16-byte vectors: multiple of
+                               1024, <= 8192 (4096)                        */
+  uint32_t ctas;            /* CTAs of the launch (0: one per SM)           */
+  uint32_t reserved;        /* must be 0                                    */
+  uint32_t reserved2;
+} cafs_batch_tuning;
+
+cafs_status cafs_batch_tuning_default(cafs_batch_tuning* tuning);
+
+/* Sorts ncols columns (host array `cols`) with one batched launch on
+ * `stream`.  The library keeps a batch workspace per (device, stream), grown
+ * on demand: about 36 MB per SM when the longest queue column has 2^20 keys,
+ * plus one all-CTA slot sized like cafs_sort's workspace.  When `reports`
+ * (host, ncols entries) is non-NULL the call waits and fills one report per
+ * column; otherwise it returns after enqueueing.  Argument errors in any
+ * column are returned before anything is enqueued. */
+cafs_status cafs_sort_batch(const cafs_column* cols, size_t ncols, cafs_report* reports,
+                            void* stream);
+/* As cafs_sort_batch with explicit knobs (NULL = defaults). */
+cafs_status cafs_sort_batch_tuned(const cafs_column* cols, size_t ncols,
+                                  const cafs_batch_tuning* tuning, cafs_report* reports,
+                                  void* stream);
+
+/* A batch plan: the columns, a workspace of its own and a CUDA graph holding
+ * the launch (and the memsets that zero its control words), recorded once on
+ * the current device.  Every cafs_batch_plan_launch replays the graph on
+ * `stream`, sorting the same column buffers again (refill them in place
+ * between launches).  Launches of one plan must not overlap on the GPU.
+ * cafs_batch_plan_reports waits for `stream` and fills ncols reports (host)
+ * for the last launch. */
+typedef struct cafs_batch_plan cafs_batch_plan;
+cafs_status cafs_batch_plan_create(const cafs_column* cols, size_t ncols,
+                                   const cafs_batch_tuning* tuning, cafs_batch_plan** plan);
+cafs_status cafs_batch_plan_launch(cafs_batch_plan* plan, void* stream);
+cafs_status cafs_batch_plan_reports(cafs_batch_plan* plan, cafs_report* reports, void* stream);
+size_t cafs_batch_plan_columns(const cafs_batch_plan* plan);
+void cafs_batch_plan_destroy(cafs_batch_plan* plan);
 
 /* Testing hooks (no counterpart in the paper).  `flags` bit 0 makes CTA 0 of
  * the next pipeline launches skip the first grid barrier, so that the other

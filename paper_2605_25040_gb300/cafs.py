@@ -51,6 +51,32 @@ class Report(ctypes.Structure):
                 "device_status": self.device_status, "timeline_ns": list(self.timeline_ns)}
 
 
+class Column(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_size_t),
+                ("dtype", ctypes.c_int), ("reserved", ctypes.c_int32)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("grid_min_n", ctypes.c_uint64), ("defer_min_n", ctypes.c_uint64),
+                ("local_slots_max", ctypes.c_uint32), ("replicas_max", ctypes.c_uint32),
+                ("emit_tile_vec", ctypes.c_uint32), ("ctas", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("reserved2", ctypes.c_uint32)]
+
+    KNOBS = ("grid_min_n", "defer_min_n", "local_slots_max", "replicas_max", "emit_tile_vec", "ctas")
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f in self.KNOBS}
+
+    @classmethod
+    def from_dict(cls, d: dict | None) -> "BatchTuning":
+        t = cls()
+        for k, v in (d or {}).items():
+            if k not in cls.KNOBS:
+                raise KeyError(f"unknown batch tuning knob {k!r}")
+            setattr(t, k, int(v))
+        return t
+
+
 class CafsError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
@@ -72,6 +98,18 @@ SIGNATURES = {
                                       ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
     "cafs_sort_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                          ctypes.c_void_p]),
+    "cafs_batch_tuning_default": (ctypes.c_int, [ctypes.POINTER(BatchTuning)]),
+    "cafs_sort_batch": (ctypes.c_int, [ctypes.POINTER(Column), ctypes.c_size_t, ctypes.POINTER(Report),
+                                       ctypes.c_void_p]),
+    "cafs_sort_batch_tuned": (ctypes.c_int, [ctypes.POINTER(Column), ctypes.c_size_t,
+                                             ctypes.POINTER(BatchTuning), ctypes.POINTER(Report),
+                                             ctypes.c_void_p]),
+    "cafs_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(Column), ctypes.c_size_t,
+                                              ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_void_p)]),
+    "cafs_batch_plan_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "cafs_batch_plan_reports": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
+    "cafs_batch_plan_columns": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "cafs_batch_plan_destroy": (None, [ctypes.c_void_p]),
     "cafs_set_test_hooks": (None, [ctypes.c_uint32, ctypes.c_uint64]),
     "cafs_kernel_launch_count": (ctypes.c_uint64, []),
     "cafs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -199,3 +237,96 @@ def kernel_launch_count() -> int:
 
 def path_name(code: int) -> str:
     return PATHS.get(code, str(code))
+
+
+# ---------------------------------------------------------------------------
+# Batched form.
+# ---------------------------------------------------------------------------
+def _columns(keys_list, outs):
+    n = len(keys_list)
+    if outs is not None and len(outs) != n:
+        raise ValueError("one output per column")
+    arr = (Column * max(n, 1))()
+    for i, k in enumerate(keys_list):
+        k = _device_tensor(k)
+        o = outs[i] if outs is not None else None
+        if o is None:
+            raise ValueError("missing output tensor")
+        if o.dtype != k.dtype or o.numel() != k.numel() or not o.is_contiguous():
+            raise ValueError("out must match keys in dtype and size")
+        arr[i].keys = k.data_ptr() if k.numel() else None
+        arr[i].out = o.data_ptr() if o.numel() else None
+        arr[i].n = k.numel()
+        arr[i].dtype = _dtype_code(k.dtype)
+        arr[i].reserved = 0
+    return arr
+
+
+def default_tuning() -> dict:
+    t = BatchTuning()
+    _check(load().cafs_batch_tuning_default(ctypes.byref(t)), "cafs_batch_tuning_default")
+    return t.as_dict()
+
+
+def sort_batch(keys_list, outs=None, tuning: dict | None = None, reports: bool = False, stream=None):
+    """Sorts many 1-D CUDA tensors with one batched launch.
+
+    Returns the outputs, and the per-column report dicts when ``reports``."""
+    import torch
+    lib = load()
+    if outs is None:
+        outs = [torch.empty_like(k) for k in keys_list]
+    arr = _columns(keys_list, outs)
+    n = len(keys_list)
+    reps = (Report * max(n, 1))() if reports else None
+    t = BatchTuning.from_dict(tuning) if tuning else None
+    dev = keys_list[0].device if n else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        _check(lib.cafs_sort_batch_tuned(arr, n, ctypes.byref(t) if t is not None else None,
+                                         reps, _stream_handle(stream)), "cafs_sort_batch")
+    if reports:
+        return outs, [reps[i].as_dict() for i in range(n)]
+    return outs
+
+
+class BatchPlan:
+    """A recorded batched launch (CUDA graph) over fixed column buffers."""
+
+    def __init__(self, keys_list, outs, tuning: dict | None = None):
+        import torch
+        self._lib = load()
+        self.keys = list(keys_list)
+        self.outs = list(outs)
+        self.n = len(self.keys)
+        arr = _columns(self.keys, self.outs)
+        t = BatchTuning.from_dict(tuning) if tuning else None
+        h = ctypes.c_void_p()
+        self.device = self.keys[0].device if self.n else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            _check(self._lib.cafs_batch_plan_create(arr, self.n, ctypes.byref(t) if t is not None else None,
+                                                    ctypes.byref(h)), "cafs_batch_plan_create")
+        self._h = h
+
+    def launch(self, stream=None) -> None:
+        import torch
+        with torch.cuda.device(self.device):
+            _check(self._lib.cafs_batch_plan_launch(self._h, _stream_handle(stream)), "cafs_batch_plan_launch")
+
+    def reports(self, stream=None) -> list:
+        import torch
+        reps = (Report * max(self.n, 1))()
+        with torch.cuda.device(self.device):
+            _check(self._lib.cafs_batch_plan_reports(self._h, reps, _stream_handle(stream)),
+                   "cafs_batch_plan_reports")
+        return [reps[i].as_dict() for i in range(self.n)]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.cafs_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

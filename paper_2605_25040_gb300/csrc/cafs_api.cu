@@ -164,7 +164,7 @@ Workspace* workspace_for(int dev, cudaStream_t s) {
   return w;
 }
 
-cafs_status check_args(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out) {
+cafs_status check_args_impl(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out) {
   if (dtype != CAFS_INT32 && dtype != CAFS_INT64) return CAFS_ERR_UNSUPPORTED_DTYPE;
   if (n == 0) return CAFS_OK;
   if ((unsigned long long)n > 0xFFFFFFFFull) return CAFS_ERR_TOO_LARGE;
@@ -222,6 +222,9 @@ cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* o
   p.gen = ++w->gen;
   p.mode = mode;
   p.test_flags = g_test_flags;
+  p.local_slots_max = kLocalSlotsMax;
+  p.replicas_max = kDefaultReplicasMax;
+  p.emit_tile_vec = kEmitTileVecDefault;
   p.timeout_ns = g_timeout_ns;
   cudaError_t e;
   if (n < kSmallN) {
@@ -245,7 +248,7 @@ cafs_status read_record(Workspace* w, cudaStream_t s, Record* r) {
   return CAFS_OK;
 }
 
-void fill_report(const Record& r, cafs_report* rep) {
+void fill_report_impl(const Record& r, cafs_report* rep) {
   std::memset(rep, 0, sizeof(*rep));
   fill_estimate(r, &rep->est);
   rep->path = (cafs_path)r.path;
@@ -256,7 +259,7 @@ void fill_report(const Record& r, cafs_report* rep) {
 
 cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, cafs_report* report,
                       void* stream) {
-  cafs_status st = check_args(keys, n, dtype, out, true);
+  cafs_status st = check_args_impl(keys, n, dtype, out, true);
   if (st != CAFS_OK) return st;
   if (n == 0) {
     if (report) {
@@ -278,12 +281,23 @@ cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, c
   if (report) {
     Record r;
     if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
-    fill_report(r, report);
+    fill_report_impl(r, report);
   }
   return CAFS_OK;
 }
 
 }  // namespace
+
+void count_launches(unsigned k) { g_launches += k; }
+unsigned long long wait_timeout_ns() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return g_timeout_ns;
+}
+cafs_status check_args(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out) {
+  return check_args_impl(keys, n, dtype, out, need_out);
+}
+void fill_report(const Record& r, cafs_report* rep) { fill_report_impl(r, rep); }
+
 }  // namespace cafs
 
 using namespace cafs;
@@ -302,7 +316,7 @@ cafs_status cafs_sort_ex(const void* keys, size_t n, cafs_dtype dtype, void* out
 cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype, cafs_estimate* est,
                             void* stream) {
   if (!est) return CAFS_ERR_INVALID_ARGUMENT;
-  cafs_status st = check_args(keys, n, dtype, nullptr, false);
+  cafs_status st = check_args_impl(keys, n, dtype, nullptr, false);
   if (st != CAFS_OK) return st;
   std::memset(est, 0, sizeof(*est));
   if (n == 0) {
@@ -327,7 +341,7 @@ cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype, cafs_e
 
 cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype, void* host_out,
                            cafs_report* report, void* stream) {
-  cafs_status st = check_args(host_keys, n, dtype, host_out, false);
+  cafs_status st = check_args_impl(host_keys, n, dtype, host_out, false);
   if (st != CAFS_OK) return st;
   if (n && !host_out) return CAFS_ERR_INVALID_ARGUMENT;
   if (n == 0) {
@@ -351,7 +365,7 @@ cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype, vo
   if (cudaMemcpyAsync(host_out, w->io, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CAFS_ERR_CUDA;
   Record r;
   if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
-  if (report) fill_report(r, report);
+  if (report) fill_report_impl(r, report);
   return CAFS_OK;
 }
 

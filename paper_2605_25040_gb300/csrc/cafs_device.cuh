@@ -108,6 +108,11 @@ __device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// its later async-proxy (bulk copy) accesses of the same bytes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
@@ -156,7 +161,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // kDevTimeout in the control block and returns false instead of waiting on.
 // Every caller returns from the kernel when the barrier reports failure, so
 // a lost CTA ends the launch with an error status rather than a hang.
-__device__ __noinline__ bool grid_sync(Ctrl* c, unsigned& epoch, unsigned long long timeout_ns) {
+static __device__ __noinline__ bool grid_sync(Ctrl* c, unsigned& epoch, unsigned long long timeout_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {

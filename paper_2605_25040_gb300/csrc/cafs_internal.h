@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "cafs.h"
+
 namespace cafs {
 
 // Algorithm 2: number of strided samples s.
@@ -134,11 +136,24 @@ struct Params {
   unsigned long long* lookback;       // radix scratch: per-CTA digit counts and bases
   unsigned long long lookback_cap;   // words
   long long* sample_keys;            // kSamples: distinct sampled keys, ascending
-  unsigned gen;          // call generation (tags look-back words)
+  unsigned gen;          // call counter (diagnostic)
   int mode;
   unsigned test_flags;
+  // Scheduling knobs (never change a result): cap on the per-CTA shared
+  // hash table (slots, power of two in [256, kLocalSlotsMax]), cap on its
+  // counter replicas per slot (power of two in [1, 32]) and the emit tile
+  // (16-byte vectors, multiple of kThreads, <= kEmitTileVecMax).
+  unsigned local_slots_max;
+  unsigned replicas_max;
+  unsigned emit_tile_vec;
+  unsigned pad_knobs;
   unsigned long long timeout_ns;
 };
+
+// Default scheduling knobs.
+constexpr unsigned kDefaultReplicasMax = 32;
+constexpr unsigned kEmitTileVecDefault = 4096;
+constexpr unsigned kEmitTileVecMax = 8192;
 
 // ---------------------------------------------------------------------------
 // Workspace sizing shared by the host entry points.
@@ -176,12 +191,74 @@ constexpr unsigned long long lookback_words(unsigned long long /*items*/) {
   return (unsigned long long)kMaxGrid * kRadixDigits;
 }
 
-// Host-side launchers (defined in cafs_pipeline.cu).
+// ---------------------------------------------------------------------------
+// Batched form: many columns in one persistent cooperative launch.  Columns
+// with n >= grid_min_n are sorted one after another by all CTAs together;
+// the others form a work queue (longest first) from which every CTA takes
+// whole columns and sorts each alone; radix-fallback columns of that queue
+// with n >= defer_min_n are put aside and radix-sorted by all CTAs at the
+// end.
+// ---------------------------------------------------------------------------
+struct BatchColumn {
+  const void* keys;
+  void* out;
+  unsigned long long n;
+  int dtype;   // 0 int32, 1 int64
+  int pad;
+};
+
+// Byte offsets of one column workspace ("slot") and its capacities.  The
+// radix temp buffer shares its bytes with the pair arrays: a column uses
+// one or the other, never both.
+struct SlotLayout {
+  unsigned long long ctrl, tkeys, tcounts, claimed;
+  unsigned long long pka, pva, pkb, pvb, sk, sv, off, tmp, look, sample;
+  unsigned long long table_cap, pair_cap, lookback_cap, n_cap, bytes;
+};
+
+struct BatchState {     // zeroed before every batched launch
+  unsigned next;        // work-queue cursor
+  unsigned ndeferred;   // columns deferred to the all-CTA radix phase
+  unsigned status;      // first device failure (kDevOk when none)
+  unsigned pad;
+};
+
+struct BatchParams {
+  const BatchColumn* cols;
+  const unsigned* grid_items;   // columns sorted by all CTAs, in order
+  const unsigned* cta_items;    // work queue, longest column first
+  unsigned* deferred;           // >= n_cta entries
+  Record* records;              // one per column
+  BatchState* state;
+  unsigned char* grid_slot;
+  unsigned char* cta_slots;     // slot b at cta_slots + b * cta_layout.bytes
+  SlotLayout grid_layout;
+  SlotLayout cta_layout;
+  unsigned n_grid, n_cta;
+  unsigned long long defer_min_n;
+  unsigned local_slots_max, replicas_max, emit_tile_vec, pad;
+  unsigned long long timeout_ns;
+};
+
+// Slot layout for columns of up to n_max keys (either dtype) worked on by
+// up to `parts` CTAs.
+SlotLayout slot_layout(unsigned long long n_max, unsigned parts);
+
+// Host-side launchers (defined in cafs_pipeline.cu and cafs_batch.cu).
 cudaError_t launch_pipeline(const Params& p, int dtype, int grid, cudaStream_t s);
 cudaError_t launch_small(const Params& p, int dtype, cudaStream_t s);
 cudaError_t pipeline_occupancy(int dtype, int* blocks_per_sm);
 cudaError_t prepare_kernels();
 cudaError_t launch_fill_u64(unsigned long long* ptr, unsigned long long n, unsigned long long v,
                             cudaStream_t s);
+cudaError_t prepare_batch_kernel();
+cudaError_t batch_occupancy(int* blocks_per_sm);
+cudaError_t launch_batch(const BatchParams& bp, int grid, cudaStream_t s);
+
+// Shared by the host entry points (defined in cafs_api.cu).
+void count_launches(unsigned k);
+unsigned long long wait_timeout_ns();
+cafs_status check_args(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out);
+void fill_report(const Record& r, cafs_report* rep);
 
 }  // namespace cafs

@@ -141,6 +141,9 @@ extern "C" cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype 
   p.gen = ++d->gen;
   p.mode = kModeSort;
   p.test_flags = 0;
+  p.local_slots_max = kLocalSlotsMax;
+  p.replicas_max = kDefaultReplicasMax;
+  p.emit_tile_vec = kEmitTileVecDefault;
   p.timeout_ns = 1000000000ull;
 
   // The array keeps the previous call's contents: the control block must

@@ -1,0 +1,1420 @@
+// The phases of the CAFS count-and-emit frequency sort on one GB300 (sm_103a),
+// shared by the single-column kernels and the batched kernel.
+//
+// For one column of N >= 2048 keys the CTAs of a scope (the whole cooperative
+// grid, or one CTA) run the pipeline of Sec. 4.1 for
+// a column of N >= 2048 keys; phases are separated by a bounded grid barrier:
+//
+//   0  sampler + Chao1 + dispatcher record          (Alg. 2, Eq. 5, Eq. 6,
+//                                                    Alg. 3; CTA 0)
+//   1  IsMonotone full scan, only when the 1024 samples ascend (Alg. 3);
+//      a sorted column is copied through (bypass)
+//   2  count: every CTA streams its share of the column through a shared
+//      memory ring filled by bulk copies (cp.async.bulk + mbarrier) and counts
+//      it, either against the <= 8 sampled keys in registers (tiny path,
+//      Sec. 4.4) or in a per-CTA open-addressing table (main path, Sec. 4.2)
+//      that is merged into a global table hashed with Eq. 4; the global table
+//      counts distinct keys and raises the overflow guard when they exceed
+//      L = C/2 (Eq. 6, Alg. 4)
+//   3  the K' (key, count) pairs are put in key order and their counts
+//      exclusive-scanned (Alg. 4): for K' <= 4096 every CTA computes, for its
+//      share of the pairs, the rank and the run offset directly (number of
+//      smaller keys and the sum of their counts); larger K' go through an LSD
+//      radix sort followed by a two-level scan
+//   4  emit: every output tile looks up its runs and writes them with 16-byte
+//      streaming stores (the paper's fill_n per pair)
+//   R  radix fallback (the paper's pdqsort: 2*K_hat > N, or the guard fired):
+//      LSD radix sort, 8-bit digits; one histogram read for all passes, then
+//      per pass a reduce-then-scan over per-CTA digit counts and an in-order
+//      stable scatter; passes whose digit is constant are skipped.
+//
+// Columns with N < 2048 are sorted by a single CTA in shared memory
+// (Table 2: "sampling does not amortize").
+//
+// All device waits (grid barrier, mbarriers) are bounded by a
+// timeout; a wait that runs out records kDevTimeout and the launch ends early
+// after draining its own bulk copies.
+
+#pragma once
+
+#include "cafs_device.cuh"
+#include "cafs_internal.h"
+
+namespace cafs {
+
+// ---------------------------------------------------------------------------
+// Phase 0: sampler, spectrum, Chao1, Eq. 6, provisional dispatch (one CTA).
+// ---------------------------------------------------------------------------
+template <typename K>
+__device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem) {
+  using T = KeyTraits<K>;
+  // Algorithm 2's FreqSet: a 4096-slot open-addressing table in shared
+  // memory, filled with the 1024 strided samples in parallel.  The empty
+  // marker is the type minimum; samples equal to it are counted on the side.
+  constexpr int kFreqSlots = 4096;
+  long long* fkey = reinterpret_cast<long long*>(smem);                 // kFreqSlots
+  unsigned* fcnt = reinterpret_cast<unsigned*>(fkey + kFreqSlots);      // kFreqSlots
+  long long* s = reinterpret_cast<long long*>(fcnt + kFreqSlots);       // kSamples, position order
+  int* scratch = reinterpret_cast<int*>(s + kSamples);                  // kWarps + 2
+  const int t = threadIdx.x;
+  const unsigned long long n = p.n;
+  const unsigned long long stride = n / kSamples > 0 ? n / kSamples : 1ull;
+  const int ns = n < (unsigned long long)kSamples ? (int)n : kSamples;
+  const long long kmin = (long long)T::min_key();
+
+  for (int i = t; i < kFreqSlots; i += kThreads) {
+    fkey[i] = kmin;
+    fcnt[i] = 0u;
+  }
+  if (t == 0) scratch[kWarps] = 0;        // samples equal to the type minimum
+  if (t == 0) scratch[kWarps + 1] = 0;    // next free index in the distinct list
+  for (int i = t; i < kSamples; i += kThreads)
+    s[i] = i < ns ? (long long)keys[(unsigned long long)i * stride] : LLONG_MAX;
+  __syncthreads();
+  int asc = 1;
+  for (int i = t; i + 1 < ns; i += kThreads) asc &= (s[i] <= s[i + 1]);
+  const int hint = __syncthreads_and(asc);
+
+  // Linear-probe insert (Alg. 2), load <= 1/4.
+  for (int i = t; i < ns; i += kThreads) {
+    const long long x = s[i];
+    if (x == kmin) {
+      atomicAdd(scratch + kWarps, 1);
+      continue;
+    }
+    unsigned slot = (unsigned)hash_slot((unsigned long long)x, 12);
+    for (int probe = 0; probe < kFreqSlots; ++probe, slot = (slot + 1) & (kFreqSlots - 1)) {
+      const long long k = *reinterpret_cast<volatile long long*>(fkey + slot);
+      if (k == x) break;
+      if (k == kmin) {
+        const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(fkey + slot),
+                                                   (unsigned long long)kmin, (unsigned long long)x);
+        if (old == kmin || old == x) break;
+      }
+    }
+    atomicAdd(fcnt + slot, 1u);
+  }
+  __syncthreads();
+  // Spectrum: occupied slots (u), slots seen once (f1) and twice (f2).
+  int cu = 0, c1 = 0, c2 = 0;
+  for (int i = t; i < kFreqSlots; i += kThreads) {
+    const unsigned c = fcnt[i];
+    cu += c > 0u;
+    c1 += c == 1u;
+    c2 += c == 2u;
+  }
+  const int nmin = scratch[kWarps];
+  int u = block_sum(cu, scratch) + (nmin > 0);
+  const int f1 = block_sum(c1, scratch) + (nmin == 1);
+  const int f2 = block_sum(c2, scratch) + (nmin == 2);
+
+  // The distinct sample values (unordered): all of them go to the workspace
+  // (they seed the count tables), and when u <= 8 also to the record (tiny
+  // path).
+  Record& r = p.ctrl->rec;
+  for (int i = t; i < kFreqSlots + 1; i += kThreads) {
+    const bool occupied = i < kFreqSlots ? fcnt[i] > 0u : nmin > 0;
+    if (occupied) {
+      const long long v = i < kFreqSlots ? fkey[i] : kmin;
+      const int idx = atomicAdd(scratch + kWarps + 1, 1);
+      if (p.sample_keys) p.sample_keys[idx] = v;
+      if (u <= kTinyMax) r.tiny_keys[idx] = v;
+    }
+  }
+  // Tiny path: find an odd multiplier that sends the u <= 8 sampled keys to
+  // distinct buckets (Eq. 4's multiplicative hash with other multipliers).
+  __syncthreads();
+  if (u <= kTinyMax && t < 32) {
+    unsigned long long tkv[kTinyMax];
+    #pragma unroll
+    for (int j = 0; j < kTinyMax; ++j)
+      tkv[j] = j < u ? (unsigned long long)(typename T::U)(K)r.tiny_keys[j] : 0ull;
+    bool found = false;
+    for (int round = 0; round < 16 && !found; ++round) {
+      const unsigned long long m = (kPhi * (2ull * (unsigned long long)(round * 32 + t) + 1ull)) | 1ull;
+      unsigned mask = 0;
+      bool ok = true;
+      #pragma unroll
+      for (int j = 0; j < kTinyMax; ++j) {
+        if (j < u) {
+          const unsigned b = (unsigned)((tkv[j] * m) >> (64 - kTinyBucketBits));
+          ok = ok && !((mask >> b) & 1u);
+          mask |= 1u << b;
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      if (bal) {
+        if (t == __ffs(bal) - 1) {
+          r.tiny_mult = m;
+          r.tiny_hash_ok = 1;
+        }
+        found = true;
+      }
+    }
+  }
+  if (t == 0) {
+    const bool saturated = (u == kSamples);
+    const unsigned long long k_hat =
+        saturated ? n : (unsigned long long)u + ((unsigned long long)f1 * f1) / (2ull * (f2 + 1));
+    const unsigned long long cap = T::kCap;
+    unsigned long long m = bit_ceil_u64((8ull * k_hat) / cap);
+    if (m < 8) m = 8;
+    const unsigned long long upper = bit_ceil_u64((n + cap - 1) / cap);
+    if (m > upper) m = upper;
+    r.n = n;
+    r.stride = stride;
+    r.n_samples = ns;
+    r.u = u;
+    r.f1 = f1;
+    r.f2 = f2;
+    r.k_hat = k_hat;
+    r.saturated = saturated;
+    r.M = m;
+    r.C = m * cap;
+    r.L = (m * cap) / 2;
+    r.sample_nondecreasing = hint;
+    r.n_tiny = u <= kTinyMax ? u : 0;
+    int d;
+    if (k_hat <= (unsigned long long)kTinyMax && u <= kTinyMax) d = 3;   // TINY
+    else if (2ull * k_hat > n) d = 5;                                   // HIGH_ENTROPY
+    else d = 4;                                                         // MAIN
+    r.dispatch = d;
+    r.path = d;
+  }
+  __syncthreads();
+}
+
+// Which CTAs work on the current column (a compile-time policy of every
+// phase): GridScope = all CTAs of the cooperative launch, phases separated
+// by the bounded grid barrier; CtaScope = this CTA alone (the batched form's
+// per-column work items), phases separated by __syncthreads.
+struct GridScope {
+  __device__ __forceinline__ unsigned part() const { return blockIdx.x; }
+  __device__ __forceinline__ unsigned nparts() const { return gridDim.x; }
+  __device__ __forceinline__ unsigned long long gthread() const {
+    return (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  }
+  __device__ __forceinline__ unsigned long long gthreads() const {
+    return (unsigned long long)gridDim.x * blockDim.x;
+  }
+  __device__ __forceinline__ bool lead() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+  __device__ __forceinline__ bool sync(Ctrl* c, unsigned& epoch, unsigned long long timeout_ns) const {
+    return grid_sync(c, epoch, timeout_ns);
+  }
+};
+
+struct CtaScope {
+  __device__ __forceinline__ unsigned part() const { return 0u; }
+  __device__ __forceinline__ unsigned nparts() const { return 1u; }
+  __device__ __forceinline__ unsigned long long gthread() const { return threadIdx.x; }
+  __device__ __forceinline__ unsigned long long gthreads() const { return blockDim.x; }
+  __device__ __forceinline__ bool lead() const { return threadIdx.x == 0; }
+  __device__ __forceinline__ bool sync(Ctrl* c, unsigned&, unsigned long long) const {
+    __syncthreads();
+    const bool ok = !device_failed(c);
+    __syncthreads();
+    return ok;
+  }
+};
+
+// Geometry of one CTA's share of a column: `head` scalar elements before the
+// first 16-byte boundary, then whole 16-byte vectors [v0, v1) of this CTA,
+// then the ragged tail [tail0, n) handled by the last CTA.
+template <typename K>
+struct Share {
+  unsigned long long head, nvec, tail0, v0, v1;
+  template <class S>
+  __device__ Share(const K* keys, unsigned long long n, const S& sc) {
+    constexpr int VPE = KeyTraits<K>::kVec;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+    head = ((16u - (addr & 15u)) & 15u) / sizeof(K);
+    if (head > n) head = n;
+    nvec = (n - head) / VPE;
+    tail0 = head + nvec * VPE;
+    const unsigned nb = sc.nparts(), b = sc.part();
+    v0 = nvec * b / nb;
+    v1 = nvec * (b + 1) / nb;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The bulk-copy ring: this CTA's vectors of the column stream through
+// kRingStages chunks of shared memory.  Warp kConsumerWarps (the last) issues
+// cp.async.bulk copies, warps 0..kConsumerWarps-1 consume.  start() issues the
+// first kRingStages chunks (at launch, before the sampler's grid barrier);
+// run() streams the whole share through a counting functor; drain() waits for
+// copies that will not be consumed.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+template <typename K>
+struct Ring {
+  unsigned char* buf;           // kRingBytes
+  unsigned long long* full;     // kRingStages
+  unsigned long long* empty;    // kRingStages
+  const unsigned char* src;     // first byte of this CTA's vector range
+  unsigned long long total;     // bytes of this CTA's vector range
+  unsigned long long nchunks;
+  unsigned long long issued;    // producer lane only
+  bool live;
+
+  __device__ __forceinline__ bool producer() const {
+    return threadIdx.x == kConsumerWarps * 32;
+  }
+
+  template <class S>
+  __device__ void start(const Params& p, const K* keys, unsigned char* smem, const S& sc) {
+    const Share<K> sh(keys, p.n, sc);
+    buf = smem + (kPipelineSmem - kRingBytes);
+    full = reinterpret_cast<unsigned long long*>(buf - 128);
+    empty = full + kRingStages;
+    src = reinterpret_cast<const unsigned char*>(keys + sh.head) + sh.v0 * 16ull;
+    total = (sh.v1 - sh.v0) * 16ull;
+    nchunks = (total + kChunkBytes - 1) / kChunkBytes;
+    issued = 0;
+    live = true;
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kRingStages; ++s) {
+        mbar_init(full + s, 1);
+        mbar_init(empty + s, kConsumerWarps);
+      }
+      fence_mbar_init();
+    }
+    // The ring's bytes may hold an earlier phase's (or column's) generic
+    // stores: every thread fences them against the coming bulk copies.
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (producer())
+      while (issued < nchunks && issued < (unsigned long long)kRingStages) issue(issued++);
+  }
+
+  __device__ __forceinline__ unsigned bytes_of(unsigned long long ch) const {
+    const unsigned long long off = ch * (unsigned long long)kChunkBytes;
+    return (unsigned)((total - off) < (unsigned long long)kChunkBytes ? (total - off) : kChunkBytes);
+  }
+
+  __device__ __forceinline__ void issue(unsigned long long ch) {
+    const int s = (int)(ch % kRingStages);
+    const unsigned bytes = bytes_of(ch);
+    mbar_arrive_expect_tx(full + s, bytes);
+    bulk_g2s(buf + (size_t)s * kChunkBytes, src + ch * (unsigned long long)kChunkBytes, bytes, full + s);
+  }
+
+  // Waits for the copies that may still be in flight (the last kRingStages
+  // issued chunks; every earlier chunk was consumed before its stage was
+  // reused), then retires the barriers.
+  __device__ void drain(const Params& p) {
+    if (!live) return;
+    if (producer()) {
+      const unsigned long long first = issued > (unsigned long long)kRingStages ? issued - kRingStages : 0ull;
+      for (unsigned long long ch = first; ch < issued; ++ch)
+        mbar_wait(full + (ch % kRingStages), (unsigned)(ch / kRingStages) & 1u, p.timeout_ns, p.ctrl);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int s = 0; s < kRingStages; ++s) {
+        mbar_inval(full + s);
+        mbar_inval(empty + s);
+      }
+    __syncthreads();
+    live = false;
+  }
+
+  // Streams the whole share; consumers call f.chunk() on each chunk and
+  // f.single() on the scalar head/tail elements.  When `*skip` becomes
+  // non-zero the consumers stop counting (the stream still runs to its end).
+  template <typename F, class S>
+  __device__ bool run(const Params& p, const K* keys, const unsigned* skip, F& f, const S& sc) {
+    using T = KeyTraits<K>;
+    constexpr int VPE = T::kVec;
+    constexpr int kConsumers = kConsumerWarps * 32;
+    Ctrl* c = p.ctrl;
+    const unsigned long long n = p.n;
+    const Share<K> sh(keys, n, sc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool consumer = warp < kConsumerWarps;
+    const int ctid = threadIdx.x;
+    if (consumer) {
+      if (sc.part() == 0)
+        for (unsigned long long i = ctid; i < sh.head; i += kConsumers) f.single(keys[i]);
+      if (sc.part() == sc.nparts() - 1)
+        for (unsigned long long i = sh.tail0 + ctid; i < n; i += kConsumers) f.single(keys[i]);
+    }
+    bool ok = true;
+    if (!consumer) {
+      if (producer()) {
+        for (; issued < nchunks; ++issued) {
+          const int s = (int)(issued % kRingStages);
+          const unsigned k = (unsigned)(issued / kRingStages);
+          if (!mbar_wait(empty + s, (k - 1) & 1u, p.timeout_ns, c)) { ok = false; break; }
+          issue(issued);
+        }
+      }
+    } else {
+      for (unsigned long long ch = 0; ch < nchunks; ++ch) {
+        const int s = (int)(ch % kRingStages);
+        const unsigned k = (unsigned)(ch / kRingStages);
+        if (!mbar_wait(full + s, k & 1u, p.timeout_ns, c)) { ok = false; break; }
+        unsigned sk = 0;
+        if (lane == 0) sk = skip ? ld_relaxed_u32(skip) : 0u;
+        sk = __shfl_sync(0xffffffffu, sk, 0);
+        if (!sk) {
+          const unsigned nk = bytes_of(ch) / (unsigned)sizeof(K);
+          const K* ck = reinterpret_cast<const K*>(buf + (size_t)s * kChunkBytes);
+          constexpr int KPT = kVecsPerThread * VPE;
+          f.template chunk<KPT, kConsumers>(ck + ctid, nk > (unsigned)ctid ? (nk - ctid + kConsumers - 1) / kConsumers : 0u);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
+      }
+    }
+    drain(p);
+    return ok && !device_failed(c);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Phase 1: IsMonotone (Alg. 3) over the whole column; early exit on the
+// first descent found by any thread.
+// ---------------------------------------------------------------------------
+template <typename K, class S>
+__device__ void phase_monotone(const Params& p, const K* keys, const S& sc) {
+  Ctrl* c = p.ctrl;
+  const unsigned long long n = p.n;
+  const unsigned long long G = sc.gthreads();
+  const unsigned long long gt = sc.gthread();
+  unsigned iter = 0;
+  for (unsigned long long i = gt; i + 1 < n; i += G) {
+    if (((++iter) & 15u) == 0 && ld_relaxed_u32(&c->inversion)) break;
+    if (keys[i] > keys[i + 1]) {
+      atomicExch(&c->inversion, 1u);
+      break;
+    }
+  }
+}
+
+// Grid-stride copy src -> dst (both n elements of K).
+template <typename K, class S>
+__device__ void grid_copy(const K* src, K* dst, unsigned long long n, const S& sc) {
+  using T = KeyTraits<K>;
+  using V = typename T::Vec;
+  const unsigned long long G = sc.gthreads();
+  const unsigned long long gt = sc.gthread();
+  const uintptr_t as = reinterpret_cast<uintptr_t>(src), ad = reinterpret_cast<uintptr_t>(dst);
+  if (((as ^ ad) & 15u) == 0) {
+    unsigned long long head = ((16u - (ad & 15u)) & 15u) / sizeof(K);
+    if (head > n) head = n;
+    const unsigned long long nvec = (n - head) / T::kVec;
+    const V* vs = reinterpret_cast<const V*>(src + head);
+    V* vd = reinterpret_cast<V*>(dst + head);
+    for (unsigned long long i = gt; i < nvec; i += G) __stcs(vd + i, __ldcg(vs + i));
+    for (unsigned long long i = gt; i < head; i += G) dst[i] = src[i];
+    for (unsigned long long i = head + nvec * T::kVec + gt; i < n; i += G) dst[i] = src[i];
+  } else {
+    for (unsigned long long i = gt; i < n; i += G) dst[i] = __ldcg(src + i);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Global table insert (Eq. 4 hash, linear probing).  Every successful claim
+// of an empty slot increments the occupancy counter and records the slot; the
+// guard fires once more than L slots are claimed or the table is full.
+// ---------------------------------------------------------------------------
+struct GlobalTable {
+  unsigned long long* keys;
+  unsigned* counts;
+  unsigned* claimed;
+  Ctrl* ctrl;
+  unsigned long long C, L;
+  int logC;
+};
+
+__device__ __forceinline__ GlobalTable global_table(const Params& p) {
+  GlobalTable g;
+  g.keys = p.tkeys;
+  g.counts = p.tcounts;
+  g.claimed = p.claimed;
+  g.ctrl = p.ctrl;
+  g.C = p.ctrl->rec.C;
+  g.L = p.ctrl->rec.L;
+  g.logC = log2_pow2(g.C);
+  return g;
+}
+
+static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long long key64, unsigned inc) {
+  Ctrl* c = g.ctrl;
+  const unsigned long long mask = g.C - 1;
+  const unsigned long long h = hash_slot(key64, g.logC);
+  for (unsigned long long probe = 0; probe < g.C; ++probe) {
+    // Once the guard has fired the counts are discarded: stop probing.
+    if ((probe & 3ull) == 3ull && ld_relaxed_u32(&c->overflow)) return;
+    const unsigned long long slot = (h + probe) & mask;
+    const unsigned long long k = ld_relaxed_u64(g.keys + slot);
+    if (k == key64) {
+      atomicAdd(g.counts + slot, inc);
+      return;
+    }
+    if (k == kEmpty64) {
+      const unsigned long long old = atomicCAS(g.keys + slot, kEmpty64, key64);
+      if (old == kEmpty64) {
+        const unsigned idx = atomicAdd(&c->occupancy, 1u);
+        if (idx < g.C) g.claimed[idx] = (unsigned)slot;
+        atomicAdd(g.counts + slot, inc);
+        if (idx >= g.L) atomicExch(&c->overflow, 1u);
+        return;
+      }
+      if (old == key64) {
+        atomicAdd(g.counts + slot, inc);
+        return;
+      }
+    }
+  }
+  atomicExch(&c->overflow, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Phase 2: count (tiny or main).
+// ---------------------------------------------------------------------------
+
+// The CTA's shared counting table: NB buckets of kBucketSlots keys (16 bytes
+// of int32 keys or 32 bytes of int64 keys per bucket, Sec. 4.2's one-line
+// bucket), each slot with R counter replicas (lane % R) so that lanes of a
+// warp hitting the same key do not serialise.  Passed by value to the
+// non-inlined slow path so that the hot loop stays small.
+// Slots per bucket: one 16-byte shared-memory load reads a whole bucket.
+template <typename K>
+constexpr int bucket_slots() { return 16 / (int)sizeof(K); }
+
+template <typename K>
+struct LocalTable {
+  static constexpr int kBucketSlots = bucket_slots<K>();
+  K* keys;          // NB * kBucketSlots, bucket-major; nullptr: no shared table
+  unsigned* cnt;    // NB * kBucketSlots * R
+  unsigned* occ;    // distinct keys held
+  unsigned limit;   // at most this many distinct keys (half the slots)
+  int logNB, NB, R, lane_rep;
+  GlobalTable gt;
+
+  __device__ __forceinline__ unsigned home(K x) const {
+    return (unsigned)hash_slot((unsigned long long)(typename KeyTraits<K>::U)x, logNB);
+  }
+  __device__ __forceinline__ void add(unsigned slot) const {
+    atomicAdd(cnt + slot * R + lane_rep, 1u);
+  }
+};
+
+// Reads the keys of one bucket with a single 16-byte load.
+__device__ __forceinline__ void load_bucket(const long long* kb, long long* k) {
+  const longlong2 a = *reinterpret_cast<const longlong2*>(kb);
+  k[0] = a.x; k[1] = a.y;
+}
+__device__ __forceinline__ void load_bucket(const int* kb, int* k) {
+  const int4 a = *reinterpret_cast<const int4*>(kb);
+  k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+}
+
+// Slow path of one key (not the type minimum) that is not in its home
+// bucket: scan buckets from home (linear probing over buckets); a key lives
+// in the first bucket that had a free slot when it was inserted, so the scan
+// stops at the first bucket with a free slot.  Claims that slot while the
+// table holds fewer than `limit` distinct keys, else goes to the global table.
+// `inc` is 0 when the table is being seeded with the sampled keys.
+template <typename K>
+__device__ __forceinline__ void slow_insert(K x, const LocalTable<K>& t, unsigned inc) {
+  using T = KeyTraits<K>;
+  constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
+  const K kmin = T::min_key();
+  if (t.keys) {
+    unsigned b = t.home(x);
+    for (int probe = 0; probe < t.NB; ++probe, b = (b + 1) & (unsigned)(t.NB - 1)) {
+      for (int j = 0; j < kBucketSlots; ++j) {
+        K* slotp = t.keys + b * kBucketSlots + j;
+        const K k = *reinterpret_cast<volatile K*>(slotp);
+        if (k == x) {
+          if (inc) t.add(b * kBucketSlots + j);
+          return;
+        }
+        if (k == kmin) {
+          if (*reinterpret_cast<volatile unsigned*>(t.occ) >= t.limit) {
+            if (inc) global_insert(t.gt, (unsigned long long)(long long)x, inc);
+            return;
+          }
+          K old;
+          if constexpr (sizeof(K) == 8) {
+            old = (K)atomicCAS(reinterpret_cast<unsigned long long*>(slotp),
+                               (unsigned long long)kmin, (unsigned long long)x);
+          } else {
+            old = (K)atomicCAS(reinterpret_cast<unsigned*>(slotp), (unsigned)kmin, (unsigned)x);
+          }
+          if (old == kmin) atomicAdd(t.occ, 1u);
+          if (old == kmin || old == x) {
+            if (inc) t.add(b * kBucketSlots + j);
+            return;
+          }
+          // another key took the slot: carry on with the next one
+        }
+      }
+    }
+  }
+  if (inc) global_insert(t.gt, (unsigned long long)(long long)x, inc);
+}
+
+// Per-key counting of one thread.  TINY: the <= 8 sampled keys are looked
+// up through a collision-free multiplicative hash into kTinyBuckets buckets
+// and counted in this thread's own shared-memory counters (Sec. 4.4, the
+// paper's eight branchless counters).  Main path (and tiny misses): read the
+// key's home bucket and add to the matching slot's counter (Sec. 4.2's bucket
+// update).  Keys that miss are handled afterwards in one loop per chunk, so
+// that a warp's misses at different positions share one pass of the slow
+// path.  Keys equal to the type minimum (the tables' empty marker) are only
+// counted.
+template <typename K, bool TINY>
+struct KeyCounter {
+  using T = KeyTraits<K>;
+  LocalTable<K> lt;
+  // tiny path
+  unsigned long long tmult;
+  unsigned tvalid;
+  const K* tkey;        // kTinyBuckets keys by bucket
+  unsigned* tcnt;       // this thread's counters, stride kConsumerWarps*32
+  unsigned long long special;
+
+  // Fast path; returns false when the key must take the slow path.
+  __device__ __forceinline__ bool fast(K x) {
+    if constexpr (TINY) {
+      const unsigned long long ux = (unsigned long long)(typename T::U)x;
+      const unsigned b = (unsigned)((ux * tmult) >> (64 - kTinyBucketBits));
+      if (((tvalid >> b) & 1u) && tkey[b] == x) {
+        tcnt[b * (kConsumerWarps * 32)] += 1u;
+        return true;
+      }
+    }
+    if (x == T::min_key()) {
+      ++special;
+      return true;
+    }
+    if (!TINY && lt.keys) {
+      constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
+      const unsigned b = lt.home(x);
+      K k[kBucketSlots];
+      load_bucket(lt.keys + b * kBucketSlots, k);
+      int hit = -1;
+      #pragma unroll
+      for (int j = kBucketSlots - 1; j >= 0; --j)
+        if (k[j] == x) hit = j;
+      if (hit >= 0) {
+        lt.add(b * kBucketSlots + hit);
+        return true;
+      }
+    }
+    return false;
+  }
+
+  __device__ __forceinline__ void single(K x) {
+    if (!fast(x)) slow_insert<K>(x, lt, 1u);
+  }
+
+  // Keys src[0], src[STRIDE], ..., src[(cnt-1)*STRIDE] (cnt <= B) of a chunk
+  // in shared memory.
+  template <int B, int STRIDE>
+  __device__ __forceinline__ void chunk(const K* src, unsigned cnt) {
+    unsigned miss = 0;
+    #pragma unroll
+    for (int i = 0; i < B; ++i)
+      if ((unsigned)i < cnt && !fast(src[i * STRIDE])) miss |= 1u << i;
+    while (miss) {
+      const int i = __ffs(miss) - 1;
+      miss &= miss - 1;
+      slow_insert<K>(src[i * STRIDE], lt, 1u);
+    }
+  }
+};
+
+// Adds this CTA's count of type-minimum keys to the control block.
+__device__ __forceinline__ void special_out(Ctrl* c, unsigned long long special, unsigned long long* red) {
+  const unsigned long long bs = block_sum(special, red);
+  if (threadIdx.x == 0 && bs) atomicAdd(&c->special, bs);
+}
+
+template <typename K, bool TINY, class SC>
+__device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem, Ring<K>& ring,
+                            const SC& sc) {
+  using T = KeyTraits<K>;
+  Ctrl* c = p.ctrl;
+  const Record& r = c->rec;
+  const unsigned long long k_hat = r.k_hat;
+  const K kmin = T::min_key();
+  constexpr int kConsumers = kConsumerWarps * 32;
+
+  // Per-CTA shared table: S slots (power of two, load <= 1/4 when K_hat is
+  // right) with R privatised counter replicas per slot (lane % R) so that hot
+  // keys do not serialise a warp's atomics.
+  constexpr int kKeyBytes = sizeof(K);
+  int S = 256;   // slots = buckets * slots per bucket; load <= 1/4 when K_hat is right
+  const int smax = (int)p.local_slots_max;
+  while (S < smax && (unsigned long long)S < 4ull * k_hat) S <<= 1;
+  const int budget = S <= 2048 ? kSmallTableBytes : kLocalTableBytes;
+  int R = (int)p.replicas_max;
+  while (R > 1 && S * (kKeyBytes + 4 * R) > budget) R >>= 1;
+  const bool use_local = TINY || (k_hat <= (unsigned long long)smax);
+
+  // Shared memory: table (| tiny counters) | misc ... barriers | ring (top).
+  const int table_bytes = TINY ? kTinyTableBytes + kTinyBuckets * kConsumers * 4
+                               : (use_local ? S * (kKeyBytes + 4 * R) : 0);
+  unsigned char* tbase = smem;
+  K* lkeys = reinterpret_cast<K*>(tbase);
+  unsigned* lcnt = reinterpret_cast<unsigned*>(tbase + (size_t)S * kKeyBytes);
+  unsigned* tcnt = reinterpret_cast<unsigned*>(tbase + kTinyTableBytes);           // kTinyBuckets x kConsumers
+  unsigned char* mbase = smem + table_bytes;
+  unsigned* local_occ = reinterpret_cast<unsigned*>(mbase);                       // 1
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(mbase + 8);     // kWarps
+  K* tkey = reinterpret_cast<K*>(mbase + 8 + 8 * kWarps);                          // kTinyBuckets
+  static_assert(kLocalTableBytes + kMiscBytes + 128 <= kPipelineSmem - kRingBytes, "table under ring");
+  static_assert(kTinyTableBytes + kTinyBuckets * kConsumerWarps * 32 * 4 + kMiscBytes + 128 <=
+                    kPipelineSmem - kRingBytes, "tiny table under ring");
+
+  const int nt = r.n_tiny;
+  const bool tiny_hash = TINY && r.tiny_hash_ok;
+  const unsigned long long tmult = r.tiny_mult;
+  unsigned tvalid = 0;
+  if (tiny_hash) {
+    for (int j = 0; j < nt; ++j) {
+      const K kj = (K)r.tiny_keys[j];
+      tvalid |= 1u << (unsigned)(((unsigned long long)(typename T::U)kj * tmult) >> (64 - kTinyBucketBits));
+    }
+  }
+  if (use_local) {
+    for (int i = threadIdx.x; i < S; i += blockDim.x) lkeys[i] = kmin;
+    for (int i = threadIdx.x; i < S * R; i += blockDim.x) lcnt[i] = 0u;
+  }
+  if (tiny_hash) {
+    for (int i = threadIdx.x; i < kTinyBuckets * kConsumers; i += blockDim.x) tcnt[i] = 0u;
+    if (threadIdx.x < nt) {
+      const K kj = (K)r.tiny_keys[threadIdx.x];
+      tkey[((unsigned long long)(typename T::U)kj * tmult) >> (64 - kTinyBucketBits)] = kj;
+    }
+  }
+  if (threadIdx.x == 0) *local_occ = 0u;
+  __syncthreads();
+  if (!TINY && use_local) {
+    // Seed with the distinct sampled keys (counts 0), so that the frequent
+    // keys are found in their buckets from the first chunk on.
+    LocalTable<K> seed;
+    seed.keys = lkeys;
+    seed.cnt = lcnt;
+    seed.occ = local_occ;
+    seed.limit = S / 2;
+    seed.NB = S / LocalTable<K>::kBucketSlots;
+    seed.logNB = log2_pow2(S / LocalTable<K>::kBucketSlots);
+    seed.R = R;
+    seed.lane_rep = 0;
+    seed.gt = global_table(p);
+    const int u = (int)r.u;
+    for (int j = threadIdx.x; j < u; j += blockDim.x) {
+      const K kj = (K)__ldcg(p.sample_keys + j);
+      if (kj != kmin) slow_insert<K>(kj, seed, 0u);
+    }
+    __syncthreads();
+  }
+
+  const bool ok = [&]() {
+    LocalTable<K> lt;
+    lt.keys = use_local ? lkeys : nullptr;
+    lt.cnt = lcnt;
+    lt.occ = local_occ;
+    lt.limit = S / 2;
+    lt.NB = S / LocalTable<K>::kBucketSlots;
+    lt.logNB = log2_pow2(S / LocalTable<K>::kBucketSlots);
+    lt.R = R;
+    lt.lane_rep = (threadIdx.x & 31) & (R - 1);
+    lt.gt = global_table(p);
+    if (tiny_hash) {
+      KeyCounter<K, true> kc;
+      kc.lt = lt;
+      kc.tmult = tmult;
+      kc.tvalid = tvalid;
+      kc.tkey = tkey;
+      kc.tcnt = tcnt + (threadIdx.x < kConsumers ? threadIdx.x : 0);
+      kc.special = 0;
+      const bool res = ring.run(p, keys, &c->overflow, kc, sc);
+      // Tiny buckets: add up the per-thread counters, insert each sampled key.
+      for (int j = 0; j < nt; ++j) {
+        const K kj = (K)r.tiny_keys[j];
+        const unsigned b = (unsigned)(((unsigned long long)(typename T::U)kj * tmult) >> (64 - kTinyBucketBits));
+        const unsigned long long v = threadIdx.x < kConsumers ? tcnt[b * kConsumers + threadIdx.x] : 0u;
+        const unsigned long long tot = block_sum(v, red);
+        if (threadIdx.x == 0 && tot) {
+          if (kj == kmin) kc.special += tot;
+          else global_insert(lt.gt, (unsigned long long)(long long)kj, (unsigned)tot);
+        }
+      }
+      special_out(c, kc.special, red);
+      return res;
+    }
+    KeyCounter<K, false> kc;
+    kc.lt = lt;
+    kc.special = 0;
+    const bool res = ring.run(p, keys, &c->overflow, kc, sc);
+    special_out(c, kc.special, red);
+    return res;
+  }();
+
+  // Flush the shared table into the global table.
+  if (use_local) {
+    const GlobalTable g = global_table(p);
+    for (int i = threadIdx.x; i < S; i += blockDim.x) {
+      const K k = lkeys[i];
+      if (k != kmin) {
+        unsigned tot = 0;
+        for (int q = 0; q < R; ++q) tot += lcnt[i * R + q];
+        if (tot) global_insert(g, (unsigned long long)(long long)k, tot);
+      }
+    }
+  }
+  return ok;
+}
+
+// Reset the global-table slots claimed in this call: this CTA's share.
+template <class S>
+__device__ void reset_claimed(const Params& p, unsigned occ, const S& sc) {
+  const unsigned b = sc.part(), nb = sc.nparts();
+  const unsigned i0 = (unsigned)((unsigned long long)occ * b / nb);
+  const unsigned i1 = (unsigned)((unsigned long long)occ * (b + 1) / nb);
+  for (unsigned i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const unsigned slot = __ldcg(p.claimed + i);
+    p.tkeys[slot] = kEmpty64;
+    p.tcounts[slot] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Phase 3a (K' <= kRankPairs): rank and run offset of every pair, all CTAs.
+// Keys in the table are distinct, so pair i goes to position
+//   rank_i = #{j : key_j < key_i}   (+1 when the type minimum occurs)
+// and its run starts at
+//   off_i = sum of count_j over key_j < key_i   (+ count of the minimum).
+// This is the sorted order and the exclusive scan of Alg. 4 in one pass.
+// CTA b takes pairs [b*K'/G, (b+1)*K'/G); a warp per pair, lanes over j.
+// ---------------------------------------------------------------------------
+template <typename K, class S>
+__device__ void phase_rank_pairs(const Params& p, unsigned occ, unsigned long long special,
+                                 unsigned char* smem, const S& sc) {
+  using T = KeyTraits<K>;
+  const unsigned b = sc.part(), nb = sc.nparts();
+  const unsigned i0 = (unsigned)((unsigned long long)occ * b / nb);
+  const unsigned i1 = (unsigned)((unsigned long long)occ * (b + 1) / nb);
+  K* skeys = reinterpret_cast<K*>(p.skeys);
+  const unsigned long long add = special ? 1ull : 0ull;
+  if (b == 0 && threadIdx.x == 0) {
+    if (special) {
+      skeys[0] = T::min_key();
+      p.offsets[0] = 0u;
+    }
+    p.offsets[occ + add] = (unsigned)p.n;
+  }
+  if (i1 <= i0) return;
+  long long* jk = reinterpret_cast<long long*>(smem);
+  unsigned* jc = reinterpret_cast<unsigned*>(jk + kRankPairs);
+  for (unsigned j = threadIdx.x; j < occ; j += blockDim.x) {
+    const unsigned slot = __ldcg(p.claimed + j);
+    jk[j] = (long long)__ldcg(p.tkeys + slot);
+    jc[j] = __ldcg(p.tcounts + slot);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (unsigned i = i0 + warp; i < i1; i += kWarps) {
+    const long long ki = jk[i];
+    unsigned rk = 0;
+    unsigned long long off = 0;
+    for (unsigned j = lane; j < occ; j += 32) {
+      const bool lt = jk[j] < ki;
+      rk += lt ? 1u : 0u;
+      off += lt ? jc[j] : 0u;
+    }
+    rk = __reduce_add_sync(0xffffffffu, rk);
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+    if (lane == 0) {
+      skeys[rk + add] = (K)ki;
+      p.offsets[rk + add] = (unsigned)(off + special);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits, stable one-sweep passes with decoupled
+// look-back across tiles of kRadixTile items (all CTAs).
+// ---------------------------------------------------------------------------
+template <typename K>
+__device__ __forceinline__ unsigned radix_digit(K k, int shift) {
+  using T = KeyTraits<K>;
+  const typename T::U u = (typename T::U)k ^ T::kSign;
+  return (unsigned)(u >> shift) & (kRadixDigits - 1);
+}
+
+// One stable counting pass on digit `pass` (8 bits at 8*pass), all CTAs.
+// CTA b owns the contiguous tiles [b*T/G, (b+1)*T/G) and scatters them in
+// order, so each digit's output position is
+//   dstart[d] + (keys with digit d in CTAs before b) + (earlier tiles of b)
+//   + (rank within the tile).
+// (a) every CTA counts digit d over its range; (b) the CTAs scan those
+// counts (CTA b takes digits d = b, b + G, ...), with a grid barrier after
+// each step; (c) every CTA ranks each tile in shared memory (stable: a
+// per-warp match on the digit, warps in order) and writes it out.
+template <typename K, bool PAY, class S>
+__device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v, K* out_k,
+                           unsigned* out_v, unsigned long long n, int pass, unsigned char* smem,
+                           unsigned& epoch, const S& sc) {
+  Ctrl* c = p.ctrl;
+  const int shift = pass * kRadixBits;
+  const unsigned long long ntiles = (n + kRadixTile - 1) / kRadixTile;
+  const unsigned b = sc.part(), nb = sc.nparts();
+  const unsigned long long tile0 = ntiles * b / nb, tile1 = ntiles * (b + 1) / nb;
+  unsigned* cta_cnt = reinterpret_cast<unsigned*>(p.lookback);       // [nb][256]
+  unsigned* cta_base = cta_cnt + nb * kRadixDigits;                   // [nb][256]
+
+  K* stage_k = reinterpret_cast<K*>(smem);
+  unsigned* stage_v = reinterpret_cast<unsigned*>(stage_k + kRadixTile);
+  unsigned short* wcnt = reinterpret_cast<unsigned short*>(stage_v + (PAY ? kRadixTile : 0));
+  unsigned* tile_cnt = reinterpret_cast<unsigned*>(wcnt + kWarps * kRadixDigits);
+  unsigned* tile_start = tile_cnt + kRadixDigits;
+  unsigned* running = tile_start + kRadixDigits;
+  unsigned* hist = running + kRadixDigits;
+  unsigned* scratch = hist + kRadixDigits;    // kWarps
+  unsigned* scan_part = scratch + kWarps;     // kThreads
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // (a) digit counts of this CTA's range
+  if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = 0u;
+  __syncthreads();
+  {
+    const unsigned long long i0 = tile0 * kRadixTile;
+    const unsigned long long i1 = tile1 * kRadixTile < n ? tile1 * kRadixTile : n;
+    constexpr int U = 4;
+    for (unsigned long long base = i0 + threadIdx.x; base < i1; base += (unsigned long long)U * kThreads) {
+      K kk[U];
+      #pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const unsigned long long i = base + (unsigned long long)j * kThreads;
+        kk[j] = i < i1 ? __ldcg(in_k + i) : (K)0;
+      }
+      #pragma unroll
+      for (int j = 0; j < U; ++j)
+        if (base + (unsigned long long)j * kThreads < i1) atomicAdd(hist + radix_digit(kk[j], shift), 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kRadixDigits) cta_cnt[b * kRadixDigits + threadIdx.x] = hist[threadIdx.x];
+  if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+
+  // (b) exclusive scan over CTAs of each digit (this CTA's digits), offset
+  // by the digit's global start (exclusive scan of the pass histogram)
+  {
+    const unsigned v = threadIdx.x < kRadixDigits ? ld_relaxed_u32(&c->hist[pass][threadIdx.x]) : 0u;
+    unsigned tot;
+    const unsigned ex = block_exclusive_scan(v, scratch, &tot);
+    if (threadIdx.x < kRadixDigits) tile_start[threadIdx.x] = ex;   // digit starts (reused below)
+  }
+  __syncthreads();
+  for (int d = (int)b; d < kRadixDigits; d += (int)nb) {
+    const unsigned dstart = tile_start[d];
+    const unsigned v = threadIdx.x < nb ? __ldcg(cta_cnt + threadIdx.x * kRadixDigits + d) : 0u;
+    unsigned tot;
+    const unsigned ex = block_exclusive_scan(v, scratch, &tot);
+    if (threadIdx.x < nb) cta_base[threadIdx.x * kRadixDigits + d] = dstart + ex;
+  }
+  if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+
+  // (c) rank and scatter this CTA's tiles in order
+  if (threadIdx.x < kRadixDigits) running[threadIdx.x] = __ldcg(cta_base + b * kRadixDigits + threadIdx.x);
+  for (unsigned long long tile = tile0; tile < tile1; ++tile) {
+    __syncthreads();
+    const unsigned long long base = tile * kRadixTile;
+    for (int d = lane; d < kRadixDigits; d += 32) wcnt[w * kRadixDigits + d] = 0;
+    __syncwarp();
+    K key[kRadixItems];
+    unsigned rd[kRadixItems];   // rank within the warp << 16 | digit (256 = no item)
+    const unsigned long long wbase = base + (unsigned long long)w * (32 * kRadixItems) + lane;
+    #pragma unroll
+    for (int j = 0; j < kRadixItems; ++j) {
+      const unsigned long long idx = wbase + j * 32;
+      const bool valid = idx < n;
+      key[j] = valid ? __ldcg(in_k + idx) : (K)0;
+      rd[j] = valid ? radix_digit(key[j], shift) : (unsigned)kRadixDigits;
+    }
+    #pragma unroll
+    for (int j = 0; j < kRadixItems; ++j) {
+      const unsigned d = rd[j];
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      unsigned old = 0;
+      if (lane == leader && d < (unsigned)kRadixDigits) {
+        old = wcnt[w * kRadixDigits + d];
+        wcnt[w * kRadixDigits + d] = (unsigned short)(old + __popc(peers));
+      }
+      old = __shfl_sync(0xffffffffu, old, leader);
+      __syncwarp();
+      rd[j] = d | ((old + __popc(peers & lanemask_lt())) << 16);
+    }
+    __syncthreads();
+    // Per digit: exclusive scan over warps and tile total.  kScanGroups
+    // threads per digit each scan a slice of the warps, then the slices'
+    // totals are combined.
+    {
+      constexpr int kScanGroups = kThreads / kRadixDigits;
+      constexpr int kWarpsPerGroup = kWarps / kScanGroups;
+      static_assert(kScanGroups * kRadixDigits == kThreads, "scan groups");
+      const int d = threadIdx.x % kRadixDigits, g = threadIdx.x / kRadixDigits;
+      unsigned run = 0;
+      #pragma unroll
+      for (int q = g * kWarpsPerGroup; q < (g + 1) * kWarpsPerGroup; ++q) {
+        const unsigned x = wcnt[q * kRadixDigits + d];
+        wcnt[q * kRadixDigits + d] = (unsigned short)run;
+        run += x;
+      }
+      scan_part[g * kRadixDigits + d] = run;
+      __syncthreads();
+      unsigned before = 0, tot = 0;
+      #pragma unroll
+      for (int q = 0; q < kScanGroups; ++q) {
+        const unsigned v = scan_part[q * kRadixDigits + d];
+        before += q < g ? v : 0u;
+        tot += v;
+      }
+      if (g > 0) {
+        #pragma unroll
+        for (int q = g * kWarpsPerGroup; q < (g + 1) * kWarpsPerGroup; ++q)
+          wcnt[q * kRadixDigits + d] = (unsigned short)(wcnt[q * kRadixDigits + d] + before);
+      }
+      if (g == 0) tile_cnt[d] = tot;
+    }
+    __syncthreads();
+    {
+      const unsigned v = threadIdx.x < kRadixDigits ? tile_cnt[threadIdx.x] : 0u;
+      unsigned tot;
+      const unsigned ex = block_exclusive_scan(v, scratch, &tot);
+      if (threadIdx.x < kRadixDigits) tile_start[threadIdx.x] = ex;
+    }
+    __syncthreads();
+    // Scatter into shared memory in tile-sorted order.
+    #pragma unroll
+    for (int j = 0; j < kRadixItems; ++j) {
+      const unsigned d = rd[j] & 0xFFFFu;
+      if (d < (unsigned)kRadixDigits) {
+        const unsigned pos = tile_start[d] + wcnt[w * kRadixDigits + d] + (rd[j] >> 16);
+        stage_k[pos] = key[j];
+        if constexpr (PAY) stage_v[pos] = __ldcg(in_v + wbase + j * 32);
+      }
+    }
+    __syncthreads();
+    const unsigned cnt = (unsigned)((n - base) < (unsigned long long)kRadixTile ? (n - base) : kRadixTile);
+    for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const K k = stage_k[i];
+      const unsigned d = radix_digit(k, shift);
+      const unsigned long long dst = (unsigned long long)(unsigned)(running[d] + (i - tile_start[d]));
+      __stcg(out_k + dst, k);
+      if constexpr (PAY) __stcg(out_v + dst, stage_v[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x < kRadixDigits) running[threadIdx.x] += tile_cnt[threadIdx.x];
+  }
+  __syncthreads();
+  return true;
+}
+
+// Full LSD radix sort src -> dst (tmp as ping-pong), all CTAs.  Returns false
+// if a barrier failed (the caller must return).
+template <typename K, bool PAY, class S>
+__device__ bool radix_sort(const Params& p, const K* src_k, const unsigned* src_v,
+                           unsigned long long n, K* dst_k, unsigned* dst_v, K* tmp_k,
+                           unsigned* tmp_v, unsigned char* smem, unsigned& epoch,
+                           const S& sc) {
+  using T = KeyTraits<K>;
+  constexpr int NP = T::kPasses;
+  Ctrl* c = p.ctrl;
+  // Histogram of every digit of every pass (one read of the keys).
+  unsigned* sh = reinterpret_cast<unsigned*>(smem);
+  for (int i = threadIdx.x; i < NP * kRadixDigits; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  {
+    const unsigned long long G = sc.gthreads();
+    const unsigned long long gt = sc.gthread();
+    constexpr int U = 4;
+    for (unsigned long long base = gt; base < n; base += G * U) {
+      K kk[U];
+      #pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const unsigned long long i = base + (unsigned long long)j * G;
+        kk[j] = i < n ? __ldcg(src_k + i) : (K)0;
+      }
+      #pragma unroll
+      for (int j = 0; j < U; ++j) {
+        if (base + (unsigned long long)j * G < n) {
+          const typename T::U u = (typename T::U)kk[j] ^ T::kSign;
+          #pragma unroll
+          for (int q = 0; q < NP; ++q) atomicAdd(sh + q * kRadixDigits + ((u >> (q * kRadixBits)) & 0xFF), 1u);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NP * kRadixDigits; i += blockDim.x)
+    if (sh[i]) atomicAdd(&c->hist[i / kRadixDigits][i % kRadixDigits], sh[i]);
+  if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+
+  // Plan: a pass whose digit is the same for every key changes nothing.
+  int* triv = reinterpret_cast<int*>(smem);  // NP flags
+  int* plan = triv + 8;                      // [0] = count, [1..] = passes
+  if (threadIdx.x < NP) triv[threadIdx.x] = 0;
+  __syncthreads();
+  if (threadIdx.x < kRadixDigits)
+    for (int q = 0; q < NP; ++q)
+      if ((unsigned long long)ld_relaxed_u32(&c->hist[q][threadIdx.x]) == n) triv[q] = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int na = 0;
+    for (int q = 0; q < NP; ++q)
+      if (!triv[q]) plan[1 + na++] = q;
+    plan[0] = na;
+  }
+  __syncthreads();
+  const int na = plan[0];
+  unsigned active_bits = 0;  // pass indices, 4 bits each
+  for (int a = 0; a < na; ++a) active_bits |= (unsigned)plan[1 + a] << (4 * a);
+  __syncthreads();
+  // The last active pass writes dst; earlier ones alternate with tmp.  If the
+  // first pass would write over its own input (in-place), every target flips
+  // and a final copy tmp -> dst follows.
+  bool flip = false;
+  if (na > 0) {
+    const bool first_to_dst = ((na - 1) % 2) == 0;
+    if (first_to_dst && (const void*)src_k == (const void*)dst_k) flip = true;
+  }
+  const K* cur_k = src_k;
+  const unsigned* cur_v = src_v;
+  for (int a = 0; a < na; ++a) {
+    bool to_dst = ((na - 1 - a) % 2) == 0;
+    if (flip) to_dst = !to_dst;
+    K* ok_ = to_dst ? dst_k : tmp_k;
+    unsigned* ov = to_dst ? dst_v : tmp_v;
+    const int pass = (int)((active_bits >> (4 * a)) & 15u);
+    if (!radix_pass<K, PAY>(p, cur_k, cur_v, ok_, ov, n, pass, smem, epoch, sc)) return false;
+    if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+    cur_k = ok_;
+    cur_v = ov;
+  }
+  if ((const void*)cur_k != (const void*)dst_k) {
+    grid_copy<K>(cur_k, dst_k, n, sc);
+    if constexpr (PAY) {
+      const unsigned long long G = sc.gthreads();
+      const unsigned long long gt = sc.gthread();
+      for (unsigned long long i = gt; i < n; i += G) dst_v[i] = __ldcg(cur_v + i);
+    }
+    if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Scan of the sorted counts (large pair path): offsets[i] = sum of counts
+// before i; offsets[kp] = n.  Two levels with one grid barrier.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ bool grid_scan_counts(const Params& p, const unsigned* vals, unsigned long long kp,
+                                 unsigned char* smem, unsigned& epoch, const S& sc) {
+  Ctrl* c = p.ctrl;
+  unsigned long long* scratch = reinterpret_cast<unsigned long long*>(smem);
+  const unsigned b = sc.part(), nb = sc.nparts();
+  const unsigned long long i0 = kp * b / nb, i1 = kp * (b + 1) / nb;
+  unsigned long long s = 0;
+  for (unsigned long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += __ldcg(vals + i);
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) c->chunk_sums[b] = s;
+  if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+  unsigned long long base = 0;
+  for (unsigned q = threadIdx.x; q < b; q += blockDim.x) base += ld_relaxed_u64(&c->chunk_sums[q]);
+  base = block_sum(base, scratch + kWarps);
+  unsigned long long carry = base;
+  for (unsigned long long off = i0; off < i1; off += blockDim.x) {
+    const unsigned long long i = off + threadIdx.x;
+    const unsigned long long v = i < i1 ? (unsigned long long)__ldcg(vals + i) : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan(v, scratch + 2 * kWarps, &tot);
+    if (i < i1) p.offsets[i] = (unsigned)(carry + ex);
+    carry += tot;
+  }
+  if (b == 0 && threadIdx.x == 0) p.offsets[kp] = (unsigned)p.n;
+  return sc.sync(c, epoch, p.timeout_ns);
+}
+
+// ---------------------------------------------------------------------------
+// Phase 4: emit.  Output tiles of p.emit_tile_vec 16-byte vectors; each CTA
+// looks up the first and last run of each of its tiles (binary search on the
+// run offsets), stages the tile's runs in shared memory and writes the
+// vectors with streaming stores.
+// ---------------------------------------------------------------------------
+constexpr int kEmitMaxTilesPerCta = 512;
+
+// Largest j in [lo, hi] with off[j] <= x (off non-decreasing, off[lo] <= x).
+__device__ __forceinline__ unsigned long long run_of(const unsigned* off, unsigned long long lo,
+                                                     unsigned long long hi, unsigned long long x) {
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi + 1) >> 1;
+    if ((unsigned long long)__ldcg(off + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename K, class S>
+__device__ void phase_emit(const Params& p, unsigned long long npairs, unsigned char* smem,
+                           const S& sc) {
+  using T = KeyTraits<K>;
+  using V = typename T::Vec;
+  constexpr int VPE = T::kVec;
+  const K* sk = reinterpret_cast<const K*>(p.skeys);
+  const unsigned* off = p.offsets;
+  K* out = reinterpret_cast<K*>(p.out);
+  const unsigned long long n = p.n;
+  const unsigned long long last = npairs - 1;
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(out);
+  unsigned long long head = ((16u - (addr & 15u)) & 15u) / sizeof(K);
+  if (head > n) head = n;
+  const unsigned long long nvec = (n - head) / VPE;
+  const unsigned long long tail0 = head + nvec * VPE;
+  const unsigned nb = sc.nparts(), b = sc.part();
+  const unsigned long long tv = p.emit_tile_vec;
+
+  if (b == 0)
+    for (unsigned long long i = threadIdx.x; i < head; i += blockDim.x) out[i] = __ldcg(sk + run_of(off, 0, last, i));
+  if (b == nb - 1)
+    for (unsigned long long i = tail0 + threadIdx.x; i < n; i += blockDim.x) out[i] = __ldcg(sk + run_of(off, 0, last, i));
+
+  const unsigned long long ntile = (nvec + tv - 1) / tv;
+  unsigned* tj = reinterpret_cast<unsigned*>(smem);                     // 2 per local tile
+  unsigned* soff = tj + 2 * kEmitMaxTilesPerCta;                        // kEmitStagePairs + 1
+  K* skey = reinterpret_cast<K*>(soff + kEmitStagePairs + 2);           // kEmitStagePairs
+  V* vout = reinterpret_cast<V*>(out + head);
+
+  for (unsigned long long round = 0;; ++round) {
+    const unsigned long long first_tile = (unsigned long long)b + round * kEmitMaxTilesPerCta * nb;
+    if (first_tile >= ntile) break;
+    // Look up the first and last run of up to kEmitMaxTilesPerCta tiles at once.
+    for (int q = threadIdx.x; q < 2 * kEmitMaxTilesPerCta; q += blockDim.x) {
+      const unsigned long long tile = first_tile + (unsigned long long)(q >> 1) * nb;
+      if (tile < ntile) {
+        const unsigned long long vb = tile * tv;
+        const unsigned long long ve = (vb + tv < nvec) ? vb + tv : nvec;
+        const unsigned long long e = (q & 1) ? head + ve * VPE - 1 : head + vb * VPE;
+        tj[q] = (unsigned)run_of(off, 0, last, e);
+      }
+    }
+    __syncthreads();
+    for (int lt = 0; lt < kEmitMaxTilesPerCta; ++lt) {
+      const unsigned long long tile = first_tile + (unsigned long long)lt * nb;
+      if (tile >= ntile) break;
+      const unsigned long long vb = tile * tv;
+      const unsigned long long ve = (vb + tv < nvec) ? vb + tv : nvec;
+      const unsigned j0 = tj[2 * lt], j1 = tj[2 * lt + 1];
+      const unsigned m = j1 - j0 + 1;
+      if (m == 1) {
+        const V kv = splat(__ldcg(sk + j0));
+        for (unsigned long long v = vb + threadIdx.x; v < ve; v += blockDim.x) __stcs(vout + v, kv);
+      } else if (m <= (unsigned)kEmitStagePairs) {
+        for (unsigned i = threadIdx.x; i <= m; i += blockDim.x) {
+          soff[i] = (i < m) ? __ldcg(off + j0 + i) : __ldcg(off + j0 + m);
+          if (i < m) skey[i] = __ldcg(sk + j0 + i);
+        }
+        __syncthreads();
+        for (unsigned long long v = vb + threadIdx.x; v < ve; v += blockDim.x) {
+          const unsigned long long e = head + v * VPE;
+          unsigned lo = 0, hi = m - 1;
+          while (lo < hi) {
+            const unsigned mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)soff[mid] <= e) lo = mid; else hi = mid - 1;
+          }
+          K vals[VPE];
+          #pragma unroll
+          for (int q = 0; q < VPE; ++q) {
+            while (lo + 1 < m && (unsigned long long)soff[lo + 1] <= e + q) ++lo;
+            vals[q] = skey[lo];
+          }
+          __stcs(vout + v, pack(vals));
+        }
+        __syncthreads();
+      } else {
+        for (unsigned long long v = vb + threadIdx.x; v < ve; v += blockDim.x) {
+          const unsigned long long e = head + v * VPE;
+          unsigned long long j = run_of(off, j0, j1, e);
+          K vals[VPE];
+          #pragma unroll
+          for (int q = 0; q < VPE; ++q) {
+            while (j < j1 && (unsigned long long)__ldcg(off + j + 1) <= e + q) ++j;
+            vals[q] = __ldcg(sk + j);
+          }
+          __stcs(vout + v, pack(vals));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The persistent pipeline kernel (N >= 2048).
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ void mark(Ctrl* c, int i, const S& sc) {
+  if (sc.lead()) c->rec.timeline[i] = global_timer_ns();
+}
+
+// How a column's pass through column_body() ended.
+enum ColumnEnd : int {
+  kColumnDone = 0,     // output written
+  kColumnRadix = 1,    // the path ends in the LSD radix fallback, not yet run
+  kColumnFailed = 2,   // a bounded wait gave up; the status is in the record
+};
+
+// Algorithm 3 for one column of n >= 2048 keys, run by the CTAs of `sc`:
+// sample and estimate, the sortedness bypass, then the tiny or main count,
+// the pair sort and scan, and the emit.  A path that ends in the radix
+// fallback (2 K_hat > N, or the overflow guard) returns kColumnRadix with
+// the table already clean, so that the caller can run the radix sort in
+// whatever scope it chooses.  The control block must start zeroed apart
+// from the grid-barrier words.
+template <typename K, class S>
+__device__ int column_body(const Params& p, unsigned char* smem, const S& sc, unsigned& epoch) {
+  Ctrl* c = p.ctrl;
+  const K* keys = reinterpret_cast<const K*>(p.keys);
+  K* out = reinterpret_cast<K*>(p.out);
+
+  // The count phase's first chunks are on their way while part 0 samples.
+  Ring<K> ring;
+  if (p.mode == kModeSort) ring.start(p, keys, smem, sc);
+  else ring.live = false;
+
+  if (sc.part() == 0) phase_sample<K>(p, keys, smem);
+  if (!sc.sync(c, epoch, p.timeout_ns)) { ring.drain(p); return kColumnFailed; }
+  mark(c, 1, sc);
+
+  Record& r = c->rec;
+  const int hint = r.sample_nondecreasing;
+  if (hint) {
+    phase_monotone<K>(p, keys, sc);
+    if (!sc.sync(c, epoch, p.timeout_ns)) { ring.drain(p); return kColumnFailed; }
+    mark(c, 2, sc);
+    if (ld_relaxed_u32(&c->inversion) == 0u) {
+      if (sc.lead()) {
+        r.dispatch = 1;   // BYPASS_SORTED
+        r.path = 1;
+      }
+      ring.drain(p);
+      if (p.mode == kModeSort && (const void*)keys != (const void*)out) grid_copy<K>(keys, out, p.n, sc);
+      return kColumnDone;
+    }
+  }
+  if (p.mode == kModeEstimate) {
+    ring.drain(p);
+    return kColumnDone;
+  }
+
+  const int d = r.dispatch;
+  if (d != 3 && d != 4) {
+    ring.drain(p);
+    if (sc.lead()) r.path = 5;  // HIGH_ENTROPY_RADIX
+    return kColumnRadix;
+  }
+  if (d == 3) phase_count<K, true>(p, keys, smem, ring, sc);
+  else phase_count<K, false>(p, keys, smem, ring, sc);
+  if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+  mark(c, 3, sc);
+  const unsigned occ = ld_relaxed_u32(&c->occupancy);
+  const unsigned long long special = ld_relaxed_u64(&c->special);
+  const unsigned long long kp = (unsigned long long)occ + (special ? 1ull : 0ull);
+  const bool overflow = ld_relaxed_u32(&c->overflow) != 0u || kp > r.L;
+  // Sec. 4.4: the tiny counters add up to N exactly when every key is one
+  // of the u sampled keys, i.e. when the column has exactly u distinct keys.
+  int path;
+  if (d == 3) path = (!overflow && kp == (unsigned long long)r.u) ? 3 : (overflow ? 8 : 7);
+  else path = overflow ? 6 : 4;
+  if (sc.lead()) {
+    r.path = path;
+    r.k_distinct = overflow ? 0ull : kp;
+    r.n_pairs = overflow ? 0ull : kp;
+  }
+  if (overflow) {
+    // Guard fired: clear the claimed slots; the caller runs the radix sort.
+    reset_claimed(p, occ, sc);
+    return kColumnRadix;
+  }
+  if (occ <= (unsigned)kRankPairs) {
+    phase_rank_pairs<K>(p, occ, special, smem, sc);
+    if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+    mark(c, 4, sc);
+    reset_claimed(p, occ, sc);
+  } else {
+    // Gather the claimed slots into pair arrays and reset the table.
+    K* ak = reinterpret_cast<K*>(p.pkeys_a);
+    const unsigned long long G = sc.gthreads();
+    const unsigned long long gt = sc.gthread();
+    for (unsigned long long i = gt; i < occ; i += G) {
+      const unsigned slot = __ldcg(p.claimed + i);
+      ak[i] = (K)(long long)__ldcg(p.tkeys + slot);
+      p.pvals_a[i] = __ldcg(p.tcounts + slot);
+      p.tkeys[slot] = kEmpty64;
+      p.tcounts[slot] = 0u;
+    }
+    if (special && gt == 0) {
+      ak[occ] = KeyTraits<K>::min_key();
+      p.pvals_a[occ] = (unsigned)special;
+    }
+    if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+    if (!radix_sort<K, true>(p, ak, p.pvals_a, kp, reinterpret_cast<K*>(p.skeys), p.svals,
+                             reinterpret_cast<K*>(p.pkeys_b), p.pvals_b, smem, epoch, sc))
+      return kColumnFailed;
+    if (!grid_scan_counts(p, p.svals, kp, smem, epoch, sc)) return kColumnFailed;
+    mark(c, 4, sc);
+  }
+  phase_emit<K>(p, kp, smem, sc);
+  return kColumnDone;
+}
+
+// The radix fallback of a column: keys -> out through the tmp buffer.
+template <typename K, class S>
+__device__ bool column_radix(const Params& p, unsigned char* smem, const S& sc, unsigned& epoch) {
+  return radix_sort<K, false>(p, reinterpret_cast<const K*>(p.keys), nullptr, p.n,
+                              reinterpret_cast<K*>(p.out), nullptr, reinterpret_cast<K*>(p.tmp),
+                              nullptr, smem, epoch, sc);
+}
+
+// ---------------------------------------------------------------------------
+// N < 2048, one CTA: the sampler statistics are still computed for the
+// report, then IsMonotone and a shared-memory bitonic sort.
+// ---------------------------------------------------------------------------
+template <typename K>
+__device__ void small_body(const Params& p, unsigned char* smem) {
+  const K* keys = reinterpret_cast<const K*>(p.keys);
+  K* out = reinterpret_cast<K*>(p.out);
+  Record& r = p.ctrl->rec;
+  phase_sample<K>(p, keys, smem);
+  const int n = (int)p.n;
+  long long* s = reinterpret_cast<long long*>(smem);
+  for (int i = threadIdx.x; i < kSmallCap; i += blockDim.x) s[i] = i < n ? (long long)keys[i] : LLONG_MAX;
+  __syncthreads();
+  int asc = 1;
+  for (int i = threadIdx.x; i + 1 < n; i += blockDim.x) asc &= (s[i] <= s[i + 1]);
+  const int mono = __syncthreads_and(asc);
+  if (threadIdx.x == 0) {
+    r.dispatch = mono ? 1 : 2;
+    r.path = mono ? 1 : 2;
+  }
+  if (p.mode == kModeEstimate) return;
+  if (!mono) bitonic_sort_pairs(s, nullptr, kSmallCap);
+  if (!(mono && (const void*)keys == (const void*)out))
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = (K)s[i];
+  __syncthreads();
+}
+
+// The N < 2048 kernel needs the sampler's FreqSet (4096 x 12 B + samples)
+// and later the column itself (kSmallCap x 8 B).
+constexpr int kSmallSmem = 4096 * 12 + kSamples * 8 + 1024;
+static_assert(kSmallSmem >= kSmallCap * 8, "small-kernel shared memory");
+
+}  // namespace cafs

@@ -183,3 +183,142 @@ def exponential_gaps(rate: float, count: int, seed: int) -> np.ndarray:
     """Poisson-process inter-arrival times (seconds) at ``rate`` per second."""
     u = _unit_float(splitmix64(seed, count))
     return -np.log1p(-u) / rate
+
+
+def batch_specs(count: int, seed: int, n_lo: float = 1e3, n_hi: float = 1e6,
+                k_cap: float = 5e4) -> list[tuple[int, int]]:
+    """(N, K) of a batch of columns: N log-uniform in [n_lo, n_hi], K
+    log-uniform in [2, max(2, min(N/4, k_cap))]."""
+    n = log_uniform_int(n_lo, n_hi, count, seed)
+    u = _unit_float(splitmix64(seed + 1, count))
+    khi = np.maximum(np.minimum(n / 4.0, k_cap), 2.0)
+    k = np.floor(np.exp(np.log(2.0) + u * (np.log(khi) - np.log(2.0)))).astype(np.int64)
+    return [(int(a), int(max(2, b))) for a, b in zip(n, k)]
+
+
+def batch_column(n: int, k: int, index: int, seed: int, dtype=np.int64,
+                 dist: str = "zipf") -> np.ndarray:
+    """Column ``index`` of a batch (its own seed, so columns differ)."""
+    return column(n, k, dist, dtype, seed=seed * 1_000_003 + index)
+
+
+def mixed_specs(count: int = 64, n_lo: float = 1e3, n_hi: float = 3e7,
+                spill_every: int = 16) -> list[tuple[int, int, str, str]]:
+    """(N, K, dtype name, kind) of the mixed batch: dtypes alternate int32 /
+    int64, N log-spaced from n_lo to n_hi, K log-spaced from 2 to N in a
+    five-step cycle whose last step is K = N (all distinct), and every
+    ``spill_every``-th column (the last of each group) a spill-trigger
+    column."""
+    out = []
+    for i in range(count):
+        n = int(round(n_lo * (n_hi / n_lo) ** (i / max(1, count - 1))))
+        f = (i % 5) / 4.0
+        k = n if f == 1.0 else max(2, int(round(2.0 * (n / 2.0) ** f)))
+        kind = "spill" if (i % spill_every) == spill_every - 1 else "zipf"
+        out.append((n, k, "int32" if i % 2 == 0 else "int64", kind))
+    return out
+
+
+def mixed_column(n: int, k: int, dtype_name: str, kind: str, index: int, seed: int = 0) -> np.ndarray:
+    dtype = np.int32 if dtype_name == "int32" else np.int64
+    if kind == "spill":
+        return spill_trigger(n, dtype, seed=seed * 1009 + index)
+    return column(n, k, "zipf", dtype, seed=seed * 1_000_003 + index)
+
+
+# ---------------------------------------------------------------------------
+# The same generators evaluated with torch on any device (bit-identical to the
+# numpy versions above: the integer steps are exact, the Zipf table is built
+# by numpy and the uniform floats take the same 53 bits).  The benchmark uses
+# them to build its multi-GB inputs in device memory.
+# ---------------------------------------------------------------------------
+def _i64(x: int) -> int:
+    x &= _MASK64
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def _srl(t, s: int):
+    """Logical right shift of int64 bit patterns."""
+    return (t >> s) & ((1 << (64 - s)) - 1)
+
+
+def splitmix64_torch(seed: int, count: int, offset: int = 0, device="cpu"):
+    import torch
+    idx = torch.arange(offset + 1, offset + count + 1, dtype=torch.int64, device=device)
+    z = idx * _i64(int(_GAMMA)) + _i64(seed)
+    z = (z ^ _srl(z, 30)) * _i64(int(_M1))
+    z = (z ^ _srl(z, 27)) * _i64(int(_M2))
+    return z ^ _srl(z, 31)
+
+
+def _mix32_torch(x):
+    m = 0xFFFFFFFF
+    x = x ^ (x >> 16)
+    x = (x * 0x7FEB352D) & m
+    x = x ^ (x >> 15)
+    x = (x * 0x846CA68B) & m
+    return x ^ (x >> 16)
+
+
+def distinct_values_torch(k: int, seed: int, dtype=np.int64, start: int = 0, device="cpu"):
+    import torch
+    if dtype == np.int64:
+        return splitmix64_torch(seed, k, offset=start, device=device)
+    if k + start > (1 << 32):
+        raise ValueError("at most 2^32 distinct 32-bit values")
+    ctr = (torch.arange(start, start + k, dtype=torch.int64, device=device) + (seed & 0xFFFFFFFF)) & 0xFFFFFFFF
+    x = _mix32_torch(ctr)
+    return (x - ((x >> 31) << 32)).to(torch.int32)
+
+
+def column_torch(n: int, k: int, dist: str = "uniform", dtype=np.int64, seed: int = 0,
+                 s: float = 1.1, device="cpu"):
+    """``column`` evaluated with torch on ``device`` (same values)."""
+    import torch
+    base = 42 + n + k
+    if k >= n:
+        return distinct_values_torch(n, base ^ seed, dtype, device=device)
+    pal = torch.from_numpy(distinct_values(k, base ^ seed, dtype)).to(device)
+    r = splitmix64_torch(base * 31 + seed, n, device=device)
+    if dist == "uniform":
+        ranks = _srl(_srl(r, 32) * k, 32)
+    elif dist == "zipf":
+        w = 1.0 / np.power(np.arange(1, k + 1, dtype=np.float64), s)
+        cdf = np.cumsum(w)
+        cdf /= cdf[-1]
+        u = _srl(r, 11).to(torch.float64) * (1.0 / (1 << 53))
+        ranks = torch.searchsorted(torch.from_numpy(cdf).to(device), u, right=True).clamp_(max=k - 1)
+    else:
+        raise ValueError(dist)
+    return pal[ranks]
+
+
+def spill_trigger_torch(n: int, dtype=np.int64, seed: int = 0, small_set: int = 64, device="cpu"):
+    """``spill_trigger`` evaluated with torch on ``device`` (same values)."""
+    import torch
+    stride = max(1, n // 1024)
+    npos = min(1024, n)
+    pos = torch.arange(npos, dtype=torch.int64, device=device) * stride
+    small = distinct_values(small_set, 1000 + seed, dtype)
+    reps = -(-npos // small_set)
+    sample_vals = torch.from_numpy(shuffle(np.tile(small, reps)[:npos], 2000 + seed)).to(device)
+    tdt = torch.int64 if dtype == np.int64 else torch.int32
+    out = torch.empty(n, dtype=tdt, device=device)
+    mask = torch.ones(n, dtype=torch.bool, device=device)
+    mask[pos] = False
+    out[pos] = sample_vals
+    out[mask] = distinct_values_torch(n - npos, 1000 + seed, dtype, start=small_set, device=device)
+    return out
+
+
+def batch_column_torch(n: int, k: int, index: int, seed: int, dtype=np.int64, dist: str = "zipf",
+                       device="cpu"):
+    return column_torch(n, k, dist, dtype, seed=seed * 1_000_003 + index, device=device)
+
+
+def mixed_column_torch(n: int, k: int, dtype_name: str, kind: str, index: int, seed: int = 0,
+                       device="cpu"):
+    dtype = np.int32 if dtype_name == "int32" else np.int64
+    if kind == "spill":
+        return spill_trigger_torch(n, dtype, seed=seed * 1009 + index, device=device)
+    return column_torch(n, k, "zipf", dtype, seed=seed * 1_000_003 + index, device=device)

@@ -67,3 +67,40 @@ def test_names(lib):
     assert lib.cafs_path_string(8) == b"tiny_miss_main_overflow_radix"
     for code, name in cafs.PATHS.items():
         assert lib.cafs_path_string(code).decode() == name
+
+
+def test_batch_argument_errors_are_synchronous(lib):
+    buf = (ctypes.c_int64 * 64)()
+    p = ctypes.addressof(buf)
+    cols = (cafs.Column * 2)()
+    cols[0].keys, cols[0].out, cols[0].n, cols[0].dtype = p, p + 256, 8, cafs.INT64
+    cols[1].keys, cols[1].out, cols[1].n, cols[1].dtype = p + 128, p + 128, 8, 5
+    # an unsupported dtype in any column rejects the whole batch before any work
+    assert lib.cafs_sort_batch(cols, 2, None, None) == 2
+    cols[1].dtype = cafs.INT64
+    cols[1].reserved = 1
+    assert lib.cafs_sort_batch(cols, 2, None, None) == 1
+    cols[1].reserved = 0
+    cols[1].out = p + 136          # partial overlap inside one column
+    assert lib.cafs_sort_batch(cols, 2, None, None) == 4
+    cols[1].out = p + 128
+    # bad knobs
+    for bad in ({"local_slots_max": 300}, {"local_slots_max": 16384}, {"replicas_max": 3},
+                {"emit_tile_vec": 1000}, {"emit_tile_vec": 16384}, {"grid_min_n": 100}):
+        t = cafs.BatchTuning.from_dict(bad)
+        assert lib.cafs_sort_batch_tuned(cols, 2, ctypes.byref(t), None, None) == 1, bad
+        h = ctypes.c_void_p()
+        assert lib.cafs_batch_plan_create(cols, 2, ctypes.byref(t), ctypes.byref(h)) == 1, bad
+        assert not h.value
+    assert lib.cafs_sort_batch(None, 3, None, None) == 1
+    assert lib.cafs_batch_plan_create(cols, 2, None, None) == 1
+
+
+def test_batch_tuning_defaults(lib):
+    t = cafs.BatchTuning()
+    assert lib.cafs_batch_tuning_default(ctypes.byref(t)) == 0
+    d = t.as_dict()
+    assert d == {"grid_min_n": 1 << 21, "defer_min_n": 1 << 15, "local_slots_max": 8192,
+                 "replicas_max": 32, "emit_tile_vec": 4096, "ctas": 0}
+    with pytest.raises(KeyError):
+        cafs.BatchTuning.from_dict({"block": 3})
