@@ -56,6 +56,14 @@ def make_column(spec, n, seed):
     return G.column(n, min(spec["K"], n), spec["dist"], np.int64, seed=seed)
 
 
+def make_column_device(spec, n, seed, device):
+    """The same column as make_column, generated in device memory."""
+    from paper_2605_25040_gb300 import datagen as G
+    if spec["dist"] == "spill":
+        return G.spill_trigger_torch(n, np.int64, seed=seed, device=device)
+    return G.column_torch(n, min(spec["K"], n), spec["dist"], np.int64, seed=seed, device=device)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -63,6 +71,28 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary of ``kernel``, or
+    None when the kernel's sources changed since that capture."""
+    import glob
+    import re
+    from paper_2605_25040_gb300 import build as B
+    try:
+        current = B.kernel_source_hash(kernel)
+    except Exception:
+        return None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(r"traffic-record: (\{.*\})\s*$", line)
+            if not m:
+                continue
+            rec = json.loads(m.group(1))
+            if rec.get("kernel") == kernel and rec.get("source_sha256") == current:
+                rec["profile"] = os.path.relpath(path, ROOT)
+                return rec
+    return None
 
 
 class ClockSampler:
@@ -137,6 +167,130 @@ def cpu_baseline(columns, budget_s: float = 12.0) -> dict:
                       f"{t:.1f} s of numpy count-then-emit (single-threaded)"}
 
 
+def _time_ms(torch, fn, warmup=2, reps=5):
+    """Median CUDA-event time of fn() on the current stream (ms)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts), min(ts)
+
+
+def _batched_case(torch, cafs, keys, workload, tune=True):
+    """One recorded batched launch (CUDA graph) vs one cafs_sort per column;
+    the launch with default knobs and with the autotuner's knobs."""
+    import collections
+    from paper_2605_25040_gb300 import autotune
+    outs = [torch.empty_like(k) for k in keys]
+    ref = [torch.empty_like(k) for k in keys]
+    total = sum(k.numel() for k in keys)
+    nbytes = sum(k.numel() * k.element_size() for k in keys)
+
+    def per_array():
+        for k, o in zip(keys, ref):
+            cafs.sort(k, o)
+
+    per_ms, per_min = _time_ms(torch, per_array)
+    tuned = None
+    default_ms = None
+    if tune:
+        tuned = autotune.tuned(keys, outs, reps=3, rounds=2)
+        default_plan = cafs.BatchPlan(keys, outs)
+        default_ms, _ = _time_ms(torch, default_plan.launch)
+        default_plan.close()
+    plan = cafs.BatchPlan(keys, outs, tuning=tuned["tuning"] if tuned else None)
+    l0 = cafs.kernel_launch_count()
+    plan_ms, plan_min = _time_ms(torch, plan.launch)
+    launches_per_batch = (cafs.kernel_launch_count() - l0) / 7.0
+    reps = plan.reports()
+    plan.close()
+    same = all(torch.equal(a, b) for a, b in zip(outs, ref))
+    sorted_ok = all(torch.equal(o, torch.sort(k).values) for k, o in zip(keys, outs))
+    peak, _ = load_peaks()
+    return {
+        "workload": workload, "columns": len(keys), "keys": total,
+        "batched_graph": {"ms": plan_ms, "min_ms": plan_min, "gkeys_s": total / plan_ms / 1e6,
+                          "frac_hbm": 2 * nbytes / (plan_ms / 1e3) / 1e9 / peak,
+                          "kernel_launches": launches_per_batch},
+        "per_array": {"ms": per_ms, "min_ms": per_min, "gkeys_s": total / per_ms / 1e6,
+                      "kernel_launches": len(keys)},
+        "default_knobs_ms": default_ms,
+        "tuning": ({"knobs": tuned["tuning"], "cached": tuned["cached"], "trials": tuned["trials"],
+                    "tuner_default_ms": tuned["default_ms"], "tuner_best_ms": tuned["ms"]}
+                   if tuned else None),
+        "speedup": per_ms / plan_ms,
+        "verified_vs_torch_sort": bool(same and sorted_ok),
+        "paths": dict(collections.Counter(cafs.path_name(r["path"]) for r in reps)),
+        "timing": "CUDA events on the current stream, median of 5 after 2 warm-ups; inputs larger than L2",
+    }
+
+
+def bench_batched(torch, cafs):
+    from paper_2605_25040_gb300 import datagen as G
+    res = {}
+    specs = G.batch_specs(4096, seed=3)
+    keys = [G.batch_column_torch(n, k, i, 3, device="cuda") for i, (n, k) in enumerate(specs)]
+    res["batch_4096"] = _batched_case(
+        torch, cafs, keys, "4096 int64 columns, N log-uniform [1e3, 1e6], K log-uniform [2, min(N/4, 5e4)], Zipf 1.1")
+    del keys
+    mspecs = G.mixed_specs()
+    keys = [G.mixed_column_torch(n, k, t, kind, i, 0, device="cuda") for i, (n, k, t, kind) in enumerate(mspecs)]
+    res["mixed_64"] = _batched_case(
+        torch, cafs, keys, "64 columns alternating int32/int64, N log-spaced 1e3..3e7, K log-spaced 2..N "
+                           "(K = N included), 4 spill-trigger columns")
+    del keys
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_served(torch, cafs, rates=(1e3, 1e4, 1e5), budget=8 << 30, pool_size=256):
+    """Open-loop Poisson traces against the request server and the serial baseline."""
+    from paper_2605_25040_gb300 import datagen as G
+    specs = G.batch_specs(pool_size, seed=5, n_lo=1e3, n_hi=3e6, k_cap=1e5)
+    dev = [G.batch_column_torch(n, k, i, 5, device="cuda") for i, (n, k) in enumerate(specs)]
+    pin_in = [t.cpu().pin_memory() for t in dev]
+    pin_out = [torch.empty_like(t).pin_memory() for t in pin_in]
+    pool = [(a.numpy(), b.numpy()) for a, b in zip(pin_in, pin_out)]
+    srv = cafs.Server(budget)
+    out = {"budget_bytes": budget, "request_pool": f"{pool_size} int64 columns, N log-uniform [1e3, 3e6], "
+                                                   "K log-uniform [2, 1e5], Zipf 1.1 (pinned host buffers)",
+           "latency": "arrival (scheduled) to sorted keys in host memory", "rates": []}
+    try:
+        for rate in rates:
+            nreq = int(min(20000, max(2000, rate)))
+            gaps = G.exponential_gaps(rate, nreq, seed=int(rate))
+            arrivals = np.cumsum(gaps) - gaps[0]
+            pick = [(i * 7919) % pool_size for i in range(nreq)]
+            pairs = [pool[j] for j in pick]
+            keys = sum(pool[j][0].size for j in pick)
+            lat, el = srv.run_trace(pairs, arrivals)
+            st = srv.stats()
+            lat_s, el_s = cafs.serial_run_trace(pairs, arrivals)
+            out["rates"].append({
+                "rate_req_s": rate, "requests": nreq, "keys": keys,
+                "server": {"gkeys_s": keys / el / 1e9, "p50_us": float(np.percentile(lat, 50)),
+                           "p99_us": float(np.percentile(lat, 99)), "elapsed_s": el},
+                "serial": {"gkeys_s": keys / el_s / 1e9, "p50_us": float(np.percentile(lat_s, 50)),
+                           "p99_us": float(np.percentile(lat_s, 99)), "elapsed_s": el_s},
+            })
+        out["server_stats"] = srv.stats()
+    finally:
+        srv.close()
+    ok = True
+    for t, (_, o) in zip(dev, pool):
+        ok &= bool(torch.equal(torch.from_numpy(o).cuda(), torch.sort(t).values))
+    out["verified_vs_torch_sort"] = ok
+    return out
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on the host cores, bounded per step."""
     n = args.n
@@ -186,6 +340,8 @@ def main():
     ap.add_argument("--no-verify", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--columns", default="",
                     help="comma-separated subset of sweep columns (e.g. uniform_K200); default all")
     args = ap.parse_args()
@@ -218,8 +374,8 @@ def main():
         specs = [s for s in specs if s["name"] in keep]
         if not specs:
             raise SystemExit(f"no sweep column matches {args.columns}")
-    host_cols = [(s["name"], make_column(s, n, seed=seeds[s["name"]])) for s in specs]
-    dev_in = [torch.from_numpy(x).cuda() for _, x in host_cols]
+    names = [s["name"] for s in specs]
+    dev_in = [make_column_device(s, n, seeds[s["name"]], "cuda") for s in specs]
     dev_out = [torch.empty_like(t) for t in dev_in]
     stream = torch.cuda.current_stream()
 
@@ -277,7 +433,7 @@ def main():
     # branch taken per column + verification against torch.sort on the device
     sweep = []
     verified = True
-    for i, (name, x) in enumerate(host_cols):
+    for i, name in enumerate(names):
         out, rep = cafs.sort_ex(dev_in[i], dev_out[i])
         if not args.no_verify:
             ref = torch.sort(dev_in[i]).values
@@ -297,7 +453,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        pin_in = [torch.from_numpy(x).pin_memory() for _, x in host_cols]
+        pin_in = [t.cpu().pin_memory() for t in dev_in]
         pin_out = [torch.empty_like(t).pin_memory() for t in pin_in]
         for a, b in zip(pin_in, pin_out):  # warm-up (allocates the io buffer)
             cafs.sort_host_ptr(a.data_ptr(), a.numel(), torch.int64, b.data_ptr(), stream=stream)
@@ -314,13 +470,23 @@ def main():
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi,
                "api": "cafs_sort_host (pinned host buffers, blocking per column)"}
         if not args.no_verify:
-            verified &= bool(np.array_equal(pin_out[0].numpy(), np.sort(host_cols[0][1])))
+            verified &= bool(np.array_equal(pin_out[0].numpy(), np.sort(pin_in[0].numpy())))
+
+    batched = served = None
+    if rank == 0 and not args.no_batched:
+        del dev_out
+        torch.cuda.empty_cache()
+        batched = bench_batched(torch, cafs)
+    if rank == 0 and not args.no_served:
+        served = bench_served(torch, cafs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        pick = [c for c in host_cols if c[0] in ("uniform_K200", "zipf_K4096", "uniform_K4096", "uniform_K4")]
-        cpu = cpu_baseline(pick or host_cols[:2])
+        want = ("uniform_K200", "zipf_K4096", "uniform_K4096", "uniform_K4")
+        pick = [(nm, dev_in[i].cpu().numpy()) for i, nm in enumerate(names) if nm in want]
+        cpu = cpu_baseline(pick or [(names[0], dev_in[0].cpu().numpy())])
 
+    traffic = traffic_record("pipeline_kernel") if n == 30_000_000 and ncol == 19 else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -340,16 +506,24 @@ def main():
                    "l2": "inputs larger than L2 (240 MB per column), no flush",
                    "parallelism": f"replicas x{world}", "verified_vs_torch_sort": verified},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": traffic["mean_dram_bytes_per_launch"] if traffic else None,
+                     "traffic_source": traffic["profile"] if traffic else
+                     "null: pipeline_kernel sources changed since the last ncu capture",
+                     "peak_kind": peak_kind,
                      "kernel": "pipeline_kernel (whole sort, one cooperative launch per column)",
                      "algorithmic_bytes_per_launch": bytes_per_col,
                      "main_path_K_le_1e5": {"achieved": main_ach, "frac": main_ach / peak,
+                                            "traffic": traffic["main_path_mean_dram_bytes_per_launch"]
+                                            if traffic else None,
                                             "columns": [specs[i]["name"] for i in main_idx]}},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
         "sweep": sweep,
+        "batched": batched,
+        "served": served,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

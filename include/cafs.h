@@ -177,7 +177,13 @@ typedef struct {
  * result.  0 in any field selects the default (cafs_batch_tuning_default). */
 typedef struct {
   uint64_t grid_min_n;      /* all-CTA columns: n >= this (>= 2048; 2^21)  */
-  uint64_t defer_min_n;     /* set-aside radix columns: n >= this (2^15)    */
+  uint64_t defer_min_n;     /* set-aside radix columns: n >= this (0: per
+                               batch, max(2^15, queue keys / (2 * CTAs)))   */
+  uint64_t cta_table_slots; /* hash table of each per-CTA slot, slots: power
+                               of two >= 64; a queue column whose Eq. 6
+                               table is larger is set aside after sampling
+                               and sorted by all CTAs (0: large enough for
+                               the longest queue column, never sets aside) */
   uint32_t local_slots_max; /* per-CTA shared hash table cap, slots: power
                                of two in [256, 8192] (8192)                */
   uint32_t replicas_max;    /* counter replicas per shared slot: power of
@@ -193,8 +199,11 @@ cafs_status cafs_batch_tuning_default(cafs_batch_tuning* tuning);
 
 /* Sorts ncols columns (host array `cols`) with one batched launch on
  * `stream`.  The library keeps a batch workspace per (device, stream), grown
- * on demand: about 36 MB per SM when the longest queue column has 2^20 keys,
- * plus one all-CTA slot sized like cafs_sort's workspace.  When `reports`
+ * on demand: per SM one slot (a 16-byte-per-slot hash table, its pair
+ * arrays and a radix buffer for columns shorter than defer_min_n; about
+ * 37 MB for a longest queue column of 2^20 keys, less with
+ * cta_table_slots), plus one all-CTA slot sized like cafs_sort's workspace
+ * for the longest column.  When `reports`
  * (host, ncols entries) is non-NULL the call waits and fills one report per
  * column; otherwise it returns after enqueueing.  Argument errors in any
  * column are returned before anything is enqueued. */
@@ -219,6 +228,84 @@ cafs_status cafs_batch_plan_launch(cafs_batch_plan* plan, void* stream);
 cafs_status cafs_batch_plan_reports(cafs_batch_plan* plan, cafs_report* reports, void* stream);
 size_t cafs_batch_plan_columns(const cafs_batch_plan* plan);
 void cafs_batch_plan_destroy(cafs_batch_plan* plan);
+
+/* Autotuner measurement step: for each of the ncand knob settings, records a
+ * plan over `cols`, launches it once to warm up and `reps` more times on
+ * `stream` (CUDA events around each launch), and stores the median launch
+ * time in ms[c]; *best = the index of the fastest.  The columns are sorted
+ * (1 + reps) * ncand times; results never depend on the knobs.  Blocking. */
+cafs_status cafs_batch_autotune(const cafs_column* cols, size_t ncols,
+                                const cafs_batch_tuning* candidates, size_t ncand, int reps,
+                                double* ms, size_t* best, void* stream);
+
+/* ---- Served form (no counterpart in the paper) ------------------------------
+ * A request server on the current device.  At creation it reserves its
+ * whole device-memory budget once: the batched kernel's workspace for
+ * max_batch_columns requests of up to max_request_keys keys, and an arena
+ * for request buffers (the rest of the budget).  Requests (host buffers) are
+ * admitted first come first served whenever their keys fit in the arena;
+ * everything admitted while the previous launch runs is sorted by the next
+ * batched launch (continuous batching).  A request's keys stay in one arena
+ * buffer from the copy in to the copy out; the buffer is released when the
+ * sorted keys are in host_out.  Server threads do the copies and launches;
+ * all entry points are thread-safe. */
+typedef struct {
+  uint32_t max_batch_columns;  /* requests per batched launch (1024)        */
+  uint32_t max_inflight;       /* batched launches in flight (3)            */
+  uint64_t max_request_keys;   /* longest request accepted (2^22)           */
+  cafs_batch_tuning tuning;    /* knobs of the batched kernel               */
+  uint32_t reserved;           /* must be 0                                  */
+  uint32_t reserved2;
+} cafs_server_config;
+
+typedef struct {
+  uint64_t launches, completed, keys_done, pending;
+  uint64_t arena_bytes, arena_peak_bytes, workspace_bytes;
+} cafs_server_stats_t;
+
+typedef struct cafs_server cafs_server;
+
+cafs_status cafs_server_config_default(cafs_server_config* cfg);
+/* cfg may be NULL (defaults).  CAFS_ERR_OUT_OF_MEMORY when the budget does
+ * not cover the workspace plus a non-empty arena, or cannot be reserved. */
+cafs_status cafs_server_create(size_t mem_budget_bytes, const cafs_server_config* cfg,
+                               cafs_server** server);
+/* Enqueues a request: n keys of `dtype` at host_keys, sorted keys to
+ * host_out (may equal host_keys); both must stay valid until the matching
+ * cafs_server_wait returns.  Pinned host memory gives the fastest copies.
+ * n > max_request_keys (or larger than the arena): CAFS_ERR_TOO_LARGE. */
+cafs_status cafs_server_submit(cafs_server* server, const void* host_keys, size_t n, cafs_dtype dtype,
+                               void* host_out, uint64_t* ticket);
+/* Blocks until the request is done; fills the report (may be NULL) and the
+ * latency from submission to the result being in host_out (may be NULL). */
+cafs_status cafs_server_wait(cafs_server* server, uint64_t ticket, cafs_report* report,
+                             double* latency_us);
+cafs_status cafs_server_stats(cafs_server* server, cafs_server_stats_t* stats);
+void cafs_server_destroy(cafs_server* server);
+
+/* One request of a replayed trace. */
+typedef struct {
+  const void* host_keys;
+  void* host_out;
+  size_t n;
+  cafs_dtype dtype;
+  int32_t reserved;            /* must be 0                                  */
+} cafs_request;
+
+/* Open-loop replay of a request trace against a server: request i is
+ * submitted arrival_s[i] seconds (non-decreasing) after the call starts,
+ * from a native thread that waits for each arrival time; latency_us[i] is
+ * the time from that arrival time to the result being in host_out.
+ * *elapsed_s (may be NULL) = first arrival to last completion.  reports may
+ * be NULL. */
+cafs_status cafs_server_run_trace(cafs_server* server, const cafs_request* reqs, size_t nreq,
+                                  const double* arrival_s, double* latency_us, cafs_report* reports,
+                                  double* elapsed_s);
+/* The same trace served one request at a time with cafs_sort_host on
+ * `stream` (the serial baseline of the served form). */
+cafs_status cafs_serial_run_trace(const cafs_request* reqs, size_t nreq, const double* arrival_s,
+                                  double* latency_us, cafs_report* reports, double* elapsed_s,
+                                  void* stream);
 
 /* Testing hooks (no counterpart in the paper).  `flags` bit 0 makes CTA 0 of
  * the next pipeline launches skip the first grid barrier, so that the other

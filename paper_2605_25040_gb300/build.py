@@ -79,3 +79,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+
+
+
+# The translation unit of each kernel family and the headers it includes.
+KERNEL_SOURCES = {
+    "pipeline_kernel": ["paper_2605_25040_gb300/csrc/cafs_pipeline.cu", "paper_2605_25040_gb300/csrc/cafs_phases.cuh",
+                        "paper_2605_25040_gb300/csrc/cafs_device.cuh", "paper_2605_25040_gb300/csrc/cafs_internal.h"],
+    "batch_kernel": ["paper_2605_25040_gb300/csrc/cafs_batch.cu", "paper_2605_25040_gb300/csrc/cafs_batch_host.h",
+                     "paper_2605_25040_gb300/csrc/cafs_phases.cuh", "paper_2605_25040_gb300/csrc/cafs_device.cuh",
+                     "paper_2605_25040_gb300/csrc/cafs_internal.h"],
+}
+
+
+def kernel_source_hash(kernel: str, read=None) -> str:
+    """SHA-256 over the sources of one kernel family (KERNEL_SOURCES).
+    Profile summaries record it, so that a DRAM-traffic figure is reported
+    only for the code it was measured on.  ``read(relpath) -> bytes``
+    substitutes another tree (e.g. a git revision)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[kernel]:
+        data = read(rel) if read else open(os.path.join(ROOT, rel), "rb").read()
+        h.update(rel.encode() + b"\0" + data + b"\0")
+    return h.hexdigest()

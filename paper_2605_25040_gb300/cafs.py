@@ -58,11 +58,12 @@ class Column(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("grid_min_n", ctypes.c_uint64), ("defer_min_n", ctypes.c_uint64),
-                ("local_slots_max", ctypes.c_uint32), ("replicas_max", ctypes.c_uint32),
+                ("cta_table_slots", ctypes.c_uint64), ("local_slots_max", ctypes.c_uint32), ("replicas_max", ctypes.c_uint32),
                 ("emit_tile_vec", ctypes.c_uint32), ("ctas", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("reserved2", ctypes.c_uint32)]
 
-    KNOBS = ("grid_min_n", "defer_min_n", "local_slots_max", "replicas_max", "emit_tile_vec", "ctas")
+    KNOBS = ("grid_min_n", "defer_min_n", "cta_table_slots", "local_slots_max", "replicas_max",
+             "emit_tile_vec", "ctas")
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f in self.KNOBS}
@@ -75,6 +76,25 @@ class BatchTuning(ctypes.Structure):
                 raise KeyError(f"unknown batch tuning knob {k!r}")
             setattr(t, k, int(v))
         return t
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch_columns", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("max_request_keys", ctypes.c_uint64), ("tuning", BatchTuning),
+                ("reserved", ctypes.c_uint32), ("reserved2", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("launches", "completed", "keys_done", "pending", "arena_bytes",
+                                                "arena_peak_bytes", "workspace_bytes")]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("host_keys", ctypes.c_void_p), ("host_out", ctypes.c_void_p), ("n", ctypes.c_size_t),
+                ("dtype", ctypes.c_int), ("reserved", ctypes.c_int32)]
 
 
 class CafsError(RuntimeError):
@@ -110,6 +130,25 @@ SIGNATURES = {
     "cafs_batch_plan_reports": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
     "cafs_batch_plan_columns": (ctypes.c_size_t, [ctypes.c_void_p]),
     "cafs_batch_plan_destroy": (None, [ctypes.c_void_p]),
+    "cafs_batch_autotune": (ctypes.c_int, [ctypes.POINTER(Column), ctypes.c_size_t, ctypes.POINTER(BatchTuning),
+                                           ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]),
+    "cafs_server_config_default": (ctypes.c_int, [ctypes.POINTER(ServerConfig)]),
+    "cafs_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ServerConfig),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "cafs_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "cafs_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Report),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "cafs_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "cafs_server_destroy": (None, [ctypes.c_void_p]),
+    "cafs_server_run_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_size_t,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(Report), ctypes.POINTER(ctypes.c_double)]),
+    "cafs_serial_run_trace": (ctypes.c_int, [ctypes.POINTER(Request), ctypes.c_size_t,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(Report), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_void_p]),
     "cafs_set_test_hooks": (None, [ctypes.c_uint32, ctypes.c_uint64]),
     "cafs_kernel_launch_count": (ctypes.c_uint64, []),
     "cafs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -289,6 +328,23 @@ def sort_batch(keys_list, outs=None, tuning: dict | None = None, reports: bool =
     return outs
 
 
+def time_tunings(keys_list, outs, tunings: list, reps: int = 3, stream=None) -> list:
+    """Median batched-launch time (ms) of each knob setting on these columns."""
+    import torch
+    lib = load()
+    arr = _columns(keys_list, outs)
+    cand = (BatchTuning * len(tunings))()
+    for i, t in enumerate(tunings):
+        cand[i] = BatchTuning.from_dict(t)
+    ms = (ctypes.c_double * len(tunings))()
+    best = ctypes.c_size_t()
+    dev = keys_list[0].device if keys_list else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        _check(lib.cafs_batch_autotune(arr, len(keys_list), cand, len(tunings), reps, ms, ctypes.byref(best),
+                                       _stream_handle(stream)), "cafs_batch_autotune")
+    return [float(ms[i]) for i in range(len(tunings))]
+
+
 class BatchPlan:
     """A recorded batched launch (CUDA graph) over fixed column buffers."""
 
@@ -330,3 +386,117 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Served form.
+# ---------------------------------------------------------------------------
+def default_server_config() -> dict:
+    c = ServerConfig()
+    _check(load().cafs_server_config_default(ctypes.byref(c)), "cafs_server_config_default")
+    return {"max_batch_columns": c.max_batch_columns, "max_inflight": c.max_inflight,
+            "max_request_keys": c.max_request_keys, "tuning": c.tuning.as_dict()}
+
+
+def _server_config(cfg: dict | None) -> ServerConfig:
+    c = ServerConfig()
+    _check(load().cafs_server_config_default(ctypes.byref(c)), "cafs_server_config_default")
+    for k, v in (cfg or {}).items():
+        if k == "tuning":
+            for tk, tv in v.items():
+                if tk not in BatchTuning.KNOBS:
+                    raise KeyError(tk)
+                setattr(c.tuning, tk, int(tv))
+        elif k in ("max_batch_columns", "max_inflight", "max_request_keys"):
+            setattr(c, k, int(v))
+        else:
+            raise KeyError(f"unknown server option {k!r}")
+    return c
+
+
+def _requests(pairs):
+    """(host_in, host_out) numpy arrays -> ctypes request array."""
+    arr = (Request * max(len(pairs), 1))()
+    for i, (a, b) in enumerate(pairs):
+        arr[i].host_keys = a.ctypes.data if a.size else None
+        arr[i].host_out = b.ctypes.data if b.size else None
+        arr[i].n = a.size
+        arr[i].dtype = _dtype_code(a.dtype)
+        arr[i].reserved = 0
+    return arr
+
+
+class Server:
+    """Request server of the served form (native threads, fixed memory budget)."""
+
+    def __init__(self, mem_budget_bytes: int, config: dict | None = None, device=None):
+        import torch
+        self._lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        c = _server_config(config)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self._lib.cafs_server_create(mem_budget_bytes, ctypes.byref(c), ctypes.byref(h)),
+                   "cafs_server_create")
+        self._h = h
+
+    def submit(self, keys: np.ndarray, out: np.ndarray) -> int:
+        if keys.dtype != out.dtype or keys.size != out.size:
+            raise ValueError("out must match keys")
+        t = ctypes.c_uint64()
+        _check(self._lib.cafs_server_submit(self._h, keys.ctypes.data if keys.size else None, keys.size,
+                                            _dtype_code(keys.dtype), out.ctypes.data if out.size else None,
+                                            ctypes.byref(t)), "cafs_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        rep = Report()
+        lat = ctypes.c_double()
+        _check(self._lib.cafs_server_wait(self._h, ticket, ctypes.byref(rep), ctypes.byref(lat)),
+               "cafs_server_wait")
+        return rep.as_dict(), float(lat.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.cafs_server_stats(self._h, ctypes.byref(st)), "cafs_server_stats")
+        return st.as_dict()
+
+    def run_trace(self, pairs, arrival_s: np.ndarray, reports: bool = False):
+        """Open-loop replay; returns (latencies_us, elapsed_s[, reports])."""
+        n = len(pairs)
+        req = _requests(pairs)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(max(n, 1), dtype=np.float64)
+        reps = (Report * max(n, 1))() if reports else None
+        el = ctypes.c_double()
+        _check(self._lib.cafs_server_run_trace(
+            self._h, req, n, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), reps, ctypes.byref(el)), "cafs_server_run_trace")
+        if reports:
+            return lat[:n], float(el.value), [reps[i].as_dict() for i in range(n)]
+        return lat[:n], float(el.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.cafs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def serial_run_trace(pairs, arrival_s: np.ndarray, stream=None):
+    """The trace served one request at a time (cafs_sort_host); (latencies_us, elapsed_s)."""
+    lib = load()
+    n = len(pairs)
+    req = _requests(pairs)
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    lat = np.zeros(max(n, 1), dtype=np.float64)
+    el = ctypes.c_double()
+    _check(lib.cafs_serial_run_trace(req, n, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None,
+                                     ctypes.byref(el), _stream_handle(stream)), "cafs_serial_run_trace")
+    return lat[:n], float(el.value)

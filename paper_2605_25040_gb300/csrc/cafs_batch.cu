@@ -19,6 +19,7 @@
 #include <mutex>
 #include <vector>
 
+#include "cafs_batch_host.h"
 #include "cafs_phases.cuh"
 
 namespace cafs {
@@ -116,6 +117,9 @@ __device__ __forceinline__ bool run_radix(const Params& p, int dtype, unsigned c
   return dtype == 1 ? radix_call<long long, S>(p, smem, epoch) : radix_call<int, S>(p, smem, epoch);
 }
 
+// Set-aside list entries: a column index, with this bit for a whole column.
+constexpr unsigned kDeferWhole = 0x80000000u;
+
 __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ Params s_p;
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
     __syncthreads();
     int end = run_body<GridScope>(s_p, cd.dtype, smem, epoch);
     if (end == kColumnRadix) end = run_radix<GridScope>(s_p, cd.dtype, smem, epoch) ? kColumnDone : kColumnFailed;
-    const bool ok = end != kColumnFailed && grid_sync(gc, epoch, bp.timeout_ns);
+    const bool ok = end == kColumnDone && grid_sync(gc, epoch, bp.timeout_ns);
     if (blockIdx.x == 0) {
       copy_record(bp.records + col, &gc->rec);
       if (!ok) note_failure(bp, gc);
@@ -163,7 +167,11 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
       } else {
         unsigned local_epoch = 0;
         end = run_body<CtaScope>(s_p, cd.dtype, smem, local_epoch);
-        if (end == kColumnRadix) {
+        if (end == kColumnTooBig) {
+          // Its Eq. 6 table exceeds this slot's: all CTAs sort it in stage 3.
+          if (threadIdx.x == 0) bp.deferred[atomicAdd(&bp.state->ndeferred, 1u)] = col | kDeferWhole;
+          end = kColumnDone;
+        } else if (end == kColumnRadix) {
           if (cd.n >= bp.defer_min_n) {
             if (threadIdx.x == 0) bp.deferred[atomicAdd(&bp.state->ndeferred, 1u)] = col;
             end = kColumnDone;
@@ -182,15 +190,26 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
     }
   }
 
-  // Stage 3: set-aside radix columns, all CTAs together.
+  // Stage 3: set-aside columns, all CTAs together: radix-fallback columns
+  // (their record is final) and whole columns whose table was too big for a
+  // per-CTA slot (sorted from the start; their record is rewritten).
   if (!grid_sync(gc, epoch, bp.timeout_ns)) return;
   const unsigned nd = ld_relaxed_u32(&bp.state->ndeferred);
   for (unsigned j = 0; j < nd; ++j) {
-    const unsigned col = __ldcg(bp.deferred + j);
+    const unsigned entry = __ldcg(bp.deferred + j);
+    const unsigned col = entry & ~kDeferWhole;
     const BatchColumn cd = bp.cols[col];
     if (threadIdx.x == 0) s_p = column_params(cd, bp.grid_slot, bp.grid_layout, bp);
     __syncthreads();
-    const bool ok = run_radix<GridScope>(s_p, cd.dtype, smem, epoch) && grid_sync(gc, epoch, bp.timeout_ns);
+    bool ok;
+    if (entry & kDeferWhole) {
+      int end = run_body<GridScope>(s_p, cd.dtype, smem, epoch);
+      if (end == kColumnRadix) end = run_radix<GridScope>(s_p, cd.dtype, smem, epoch) ? kColumnDone : kColumnFailed;
+      ok = (end == kColumnDone) && grid_sync(gc, epoch, bp.timeout_ns);
+      if (ok && blockIdx.x == 0) copy_record(bp.records + col, &gc->rec);
+    } else {
+      ok = run_radix<GridScope>(s_p, cd.dtype, smem, epoch) && grid_sync(gc, epoch, bp.timeout_ns);
+    }
     if (!ok) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         unsigned st = ld_relaxed_u32(&gc->rec.status);
@@ -248,15 +267,13 @@ namespace {
 constexpr unsigned long long align256(unsigned long long x) { return (x + 255) & ~255ull; }
 }  // namespace
 
-SlotLayout slot_layout(unsigned long long n_max, unsigned parts) {
+SlotLayout slot_layout(unsigned long long table_cap, unsigned long long tmp_keys, unsigned parts) {
   SlotLayout L;
   std::memset(&L, 0, sizeof(L));
-  if (n_max < kSmallN) n_max = kSmallN;
-  const unsigned long long t0 = table_capacity(n_max, 0), t1 = table_capacity(n_max, 1);
-  L.table_cap = t0 > t1 ? t0 : t1;
+  L.table_cap = table_cap < 64 ? 64 : table_cap;
   L.pair_cap = pair_capacity(L.table_cap);
   L.lookback_cap = (unsigned long long)(parts ? parts : 1) * kRadixDigits;
-  L.n_cap = n_max;
+  L.n_cap = tmp_keys;
   const unsigned long long pc = L.pair_cap;
   unsigned long long o = 0;
   L.ctrl = o;    o = align256(o + sizeof(Ctrl));
@@ -274,21 +291,12 @@ SlotLayout slot_layout(unsigned long long n_max, unsigned parts) {
   L.sv = o;  o = align256(o + pc * 4);
   L.off = o; o = align256(o + (pc + 2) * 4);
   L.tmp = region;
-  const unsigned long long tmp_end = align256(region + n_max * 8);
+  const unsigned long long tmp_end = align256(region + tmp_keys * 8);
   L.bytes = o > tmp_end ? o : tmp_end;
   return L;
 }
 
-namespace {
 
-struct Tuning {
-  unsigned long long grid_min_n = 1ull << 21;
-  unsigned long long defer_min_n = 1ull << 15;
-  unsigned local_slots_max = kLocalSlotsMax;
-  unsigned replicas_max = kDefaultReplicasMax;
-  unsigned emit_tile_vec = kEmitTileVecDefault;
-  unsigned ctas = 0;   // 0: one per SM
-};
 
 cafs_status tuning_from(const cafs_batch_tuning* t, Tuning* out) {
   Tuning d;
@@ -297,6 +305,11 @@ cafs_status tuning_from(const cafs_batch_tuning* t, Tuning* out) {
     if (t->grid_min_n) d.grid_min_n = t->grid_min_n;
     if (d.grid_min_n < kSmallN) return CAFS_ERR_INVALID_ARGUMENT;
     if (t->defer_min_n) d.defer_min_n = t->defer_min_n;
+    if (t->cta_table_slots) {
+      const unsigned long long v = t->cta_table_slots;
+      if (v < 64 || (v & (v - 1))) return CAFS_ERR_INVALID_ARGUMENT;
+      d.cta_table_slots = v;
+    }
     if (t->local_slots_max) {
       const unsigned v = t->local_slots_max;
       if (v < 256 || v > (unsigned)kLocalSlotsMax || (v & (v - 1))) return CAFS_ERR_INVALID_ARGUMENT;
@@ -322,31 +335,13 @@ void tuning_to(const Tuning& d, cafs_batch_tuning* t) {
   std::memset(t, 0, sizeof(*t));
   t->grid_min_n = d.grid_min_n;
   t->defer_min_n = d.defer_min_n;
+  t->cta_table_slots = d.cta_table_slots;
   t->local_slots_max = d.local_slots_max;
   t->replicas_max = d.replicas_max;
   t->emit_tile_vec = d.emit_tile_vec;
   t->ctas = d.ctas;
 }
 
-// Device buffers of one batched launch configuration.
-struct BatchBuffers {
-  int device = -1;
-  int grid = 0;
-  SlotLayout gl{}, cl{};
-  unsigned char* grid_slot = nullptr;
-  unsigned char* cta_slots = nullptr;
-  size_t col_cap = 0;
-  BatchColumn* d_cols = nullptr;
-  unsigned* d_items = nullptr;      // grid items, then queue items
-  unsigned* d_deferred = nullptr;
-  Record* d_records = nullptr;
-  BatchState* d_state = nullptr;
-  BatchColumn* h_cols = nullptr;    // pinned staging
-  unsigned* h_items = nullptr;
-  Record* h_records = nullptr;
-  BatchState* h_state = nullptr;
-  cudaEvent_t staged = nullptr;     // the last upload from the staging buffers has run
-};
 
 void free_batch(BatchBuffers* b) {
   auto fd = [](auto*& p) { if (p) cudaFree((void*)p); p = nullptr; };
@@ -361,10 +356,6 @@ void free_batch(BatchBuffers* b) {
   b->cl = SlotLayout{};
 }
 
-struct BatchDevice {
-  bool ready = false;
-  int grid = 0;   // one CTA per SM (the batched kernel's occupancy)
-};
 std::mutex g_batch_mu;
 std::map<int, BatchDevice> g_batch_dev;
 std::map<std::pair<int, uintptr_t>, BatchBuffers*> g_batch_ws;
@@ -385,14 +376,20 @@ cafs_status batch_device(int dev, BatchDevice** out) {
   return CAFS_OK;
 }
 
-// The columns of one batch, validated and scheduled.
-struct Schedule {
-  std::vector<BatchColumn> cols;
-  std::vector<unsigned> grid_items, cta_items;
-  unsigned long long n_max_grid = 0, n_max_cta = 0;
-};
+cafs_status batch_grid(int dev, int* grid) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BatchDevice* d = nullptr;
+  const cafs_status st = batch_device(dev, &d);
+  if (st == CAFS_OK) *grid = d->grid;
+  return st;
+}
+
 
 cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t, Schedule* s) {
+  s->cols.clear();
+  s->grid_items.clear();
+  s->cta_items.clear();
+  s->n_max_grid = s->n_max_cta = s->sum_cta = 0;
   if (ncols && !cols) return CAFS_ERR_INVALID_ARGUMENT;
   if (ncols > 0xFFFFFFF0ull) return CAFS_ERR_TOO_LARGE;
   s->cols.resize(ncols);
@@ -414,6 +411,7 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
     } else {
       s->cta_items.push_back((unsigned)i);
       s->n_max_cta = std::max(s->n_max_cta, (unsigned long long)c.n);
+      s->sum_cta += c.n;
     }
   }
   // Longest first: the queue's tail ends with the shortest columns.
@@ -422,15 +420,22 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
   return CAFS_OK;
 }
 
+unsigned long long resolve_defer(const Tuning& t, const Schedule& s, int grid) {
+  if (t.defer_min_n) return t.defer_min_n;
+  const unsigned long long fair = s.sum_cta / (2ull * (unsigned long long)(grid > 0 ? grid : 1));
+  return std::max(1ull << 15, fair);
+}
+
 // Grows `b` to hold the schedule (call with g_batch_mu held, device current).
 cafs_status ensure_batch(BatchBuffers* b, int grid, const Schedule& sc, const Tuning& t,
                          cudaStream_t s) {
   const unsigned long long ncols = sc.cols.size();
-  // The all-CTA slot also radix-sorts the set-aside queue columns.
-  unsigned long long n_grid_slot = sc.n_max_grid;
-  if (sc.n_max_cta >= t.defer_min_n) n_grid_slot = std::max(n_grid_slot, sc.n_max_cta);
-  const SlotLayout gl = slot_layout(n_grid_slot, (unsigned)grid);
-  const SlotLayout cl = slot_layout(sc.n_max_cta, 1);
+  // The all-CTA slot also sorts the set-aside queue columns.
+  const unsigned long long n_grid_slot = std::max(sc.n_max_grid, sc.n_max_cta);
+  const SlotLayout gl = slot_layout(table_capacity_any(n_grid_slot), n_grid_slot, (unsigned)grid);
+  unsigned long long cta_table = table_capacity_any(sc.n_max_cta);
+  if (t.cta_table_slots && t.cta_table_slots < cta_table) cta_table = t.cta_table_slots;
+  const SlotLayout cl = slot_layout(cta_table, std::min(sc.n_max_cta, resolve_defer(t, sc, grid)), 1);
   const bool grow_grid = !b->grid_slot || gl.bytes > b->gl.bytes || gl.table_cap > b->gl.table_cap ||
                          gl.pair_cap > b->gl.pair_cap || gl.n_cap > b->gl.n_cap ||
                          gl.lookback_cap > b->gl.lookback_cap;
@@ -444,7 +449,8 @@ cafs_status ensure_batch(BatchBuffers* b, int grid, const Schedule& sc, const Tu
   if (grow_grid) {
     if (b->grid_slot) cudaFree(b->grid_slot);
     b->grid_slot = nullptr;
-    const SlotLayout L = slot_layout(std::max(n_grid_slot, b->gl.n_cap), (unsigned)grid);
+    const SlotLayout L = slot_layout(std::max(gl.table_cap, b->gl.table_cap), std::max(gl.n_cap, b->gl.n_cap),
+                                     (unsigned)grid);
     if (cudaMalloc((void**)&b->grid_slot, L.bytes) != cudaSuccess) {
       cudaGetLastError();
       b->gl = SlotLayout{};
@@ -458,7 +464,9 @@ cafs_status ensure_batch(BatchBuffers* b, int grid, const Schedule& sc, const Tu
   if (grow_cta) {
     if (b->cta_slots) cudaFree(b->cta_slots);
     b->cta_slots = nullptr;
-    const SlotLayout L = slot_layout(std::max(sc.n_max_cta, grid == b->grid ? b->cl.n_cap : 0ull), 1);
+    const bool same = grid == b->grid;
+    const SlotLayout L = slot_layout(std::max(cl.table_cap, same ? b->cl.table_cap : 0ull),
+                                     std::max(cl.n_cap, same ? b->cl.n_cap : 0ull), 1);
     if (cudaMalloc((void**)&b->cta_slots, L.bytes * (size_t)grid) != cudaSuccess) {
       cudaGetLastError();
       b->cl = SlotLayout{};
@@ -499,9 +507,10 @@ cafs_status ensure_batch(BatchBuffers* b, int grid, const Schedule& sc, const Tu
 
 // Copies the schedule to the device buffers (asynchronously on s).
 cafs_status upload(BatchBuffers* b, const Schedule& sc, cudaStream_t s) {
-  if (cudaEventSynchronize(b->staged) != cudaSuccess) return CAFS_ERR_CUDA;  // staging free again
   const size_t ncols = sc.cols.size();
   const size_t nitems = sc.grid_items.size() + sc.cta_items.size();
+  if (ncols > b->col_cap || nitems > ncols) return CAFS_ERR_INTERNAL;
+  if (cudaEventSynchronize(b->staged) != cudaSuccess) return CAFS_ERR_CUDA;  // staging free again
   if (ncols) std::memcpy(b->h_cols, sc.cols.data(), ncols * sizeof(BatchColumn));
   if (!sc.grid_items.empty())
     std::memcpy(b->h_items, sc.grid_items.data(), sc.grid_items.size() * sizeof(unsigned));
@@ -530,7 +539,8 @@ BatchParams make_params(const BatchBuffers* b, const Schedule& sc, const Tuning&
   bp.cta_layout = b->cl;
   bp.n_grid = (unsigned)sc.grid_items.size();
   bp.n_cta = (unsigned)sc.cta_items.size();
-  bp.defer_min_n = t.defer_min_n;
+  // A queue column sorted by its own CTA's radix must fit the slot's buffer.
+  bp.defer_min_n = std::min(resolve_defer(t, sc, b->grid), b->cl.n_cap + 1);
   bp.local_slots_max = t.local_slots_max;
   bp.replicas_max = t.replicas_max;
   bp.emit_tile_vec = t.emit_tile_vec;
@@ -573,7 +583,6 @@ cafs_status read_reports(BatchBuffers* b, const Schedule& sc, cafs_report* repor
   return CAFS_OK;
 }
 
-}  // namespace
 }  // namespace cafs
 
 using namespace cafs;
@@ -654,12 +663,7 @@ cafs_status cafs_batch_plan_create(const cafs_column* cols, size_t ncols, const 
   if (cudaGetDevice(&dev) != cudaSuccess) return fail(CAFS_ERR_CUDA);
   pl->device = dev;
   int grid = 0;
-  {
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    BatchDevice* d = nullptr;
-    if ((st = batch_device(dev, &d)) != CAFS_OK) return fail(st);
-    grid = d->grid;
-  }
+  if ((st = batch_grid(dev, &grid)) != CAFS_OK) return fail(st);
   if (pl->tuning.ctas && (int)pl->tuning.ctas < grid) grid = (int)pl->tuning.ctas;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(CAFS_ERR_CUDA);
   if ((st = ensure_batch(&pl->buf, grid, pl->sched, pl->tuning, s)) != CAFS_OK) return fail(st);
@@ -705,6 +709,48 @@ cafs_status cafs_batch_plan_reports(cafs_batch_plan* pl, cafs_report* reports, v
 }
 
 size_t cafs_batch_plan_columns(const cafs_batch_plan* pl) { return pl ? pl->sched.cols.size() : 0; }
+
+cafs_status cafs_batch_autotune(const cafs_column* cols, size_t ncols, const cafs_batch_tuning* candidates,
+                                size_t ncand, int reps, double* ms, size_t* best, void* stream) {
+  if (!candidates || ncand == 0 || reps < 1 || !ms || !best) return CAFS_ERR_INVALID_ARGUMENT;
+  for (size_t c = 0; c < ncand; ++c) {
+    Tuning t;
+    cafs_status st = tuning_from(&candidates[c], &t);
+    if (st != CAFS_OK) return st;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CAFS_ERR_CUDA;
+  cafs_status st = CAFS_OK;
+  double best_ms = 0.0;
+  std::vector<double> times;
+  for (size_t c = 0; c < ncand && st == CAFS_OK; ++c) {
+    cafs_batch_plan* pl = nullptr;
+    st = cafs_batch_plan_create(cols, ncols, &candidates[c], &pl);
+    if (st != CAFS_OK) break;
+    times.clear();
+    for (int r = 0; r <= reps && st == CAFS_OK; ++r) {   // launch 0 warms up
+      if (cudaEventRecord(e0, s) != cudaSuccess) st = CAFS_ERR_CUDA;
+      if (st == CAFS_OK) st = cafs_batch_plan_launch(pl, stream);
+      if (st == CAFS_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        st = CAFS_ERR_CUDA;
+      float t = 0.f;
+      if (st == CAFS_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = CAFS_ERR_CUDA;
+      if (st == CAFS_OK && r > 0) times.push_back(t);
+    }
+    cafs_batch_plan_destroy(pl);
+    if (st != CAFS_OK) break;
+    std::sort(times.begin(), times.end());
+    ms[c] = times[times.size() / 2];
+    if (c == 0 || ms[c] < best_ms) {
+      best_ms = ms[c];
+      *best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
 
 void cafs_batch_plan_destroy(cafs_batch_plan* pl) {
   if (!pl) return;

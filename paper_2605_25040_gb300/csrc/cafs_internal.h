@@ -209,7 +209,9 @@ struct BatchColumn {
 
 // Byte offsets of one column workspace ("slot") and its capacities.  The
 // radix temp buffer shares its bytes with the pair arrays: a column uses
-// one or the other, never both.
+// one or the other, never both.  A per-CTA slot may hold a smaller table
+// than its longest column could need (Eq. 6); such a column is set aside
+// after sampling and sorted by all CTAs.
 struct SlotLayout {
   unsigned long long ctrl, tkeys, tcounts, claimed;
   unsigned long long pka, pva, pkb, pvb, sk, sv, off, tmp, look, sample;
@@ -240,9 +242,14 @@ struct BatchParams {
   unsigned long long timeout_ns;
 };
 
-// Slot layout for columns of up to n_max keys (either dtype) worked on by
-// up to `parts` CTAs.
-SlotLayout slot_layout(unsigned long long n_max, unsigned parts);
+// Slot layout: a hash table of table_cap slots (with pair arrays for its
+// L + 1 pairs), a radix temp buffer of tmp_keys keys (either dtype), radix
+// scratch for up to `parts` CTAs.
+SlotLayout slot_layout(unsigned long long table_cap, unsigned long long tmp_keys, unsigned parts);
+// Largest table any column of up to n keys can need (either dtype).
+constexpr unsigned long long table_capacity_any(unsigned long long n) {
+  return table_capacity(n, 0) > table_capacity(n, 1) ? table_capacity(n, 0) : table_capacity(n, 1);
+}
 
 // Host-side launchers (defined in cafs_pipeline.cu and cafs_batch.cu).
 cudaError_t launch_pipeline(const Params& p, int dtype, int grid, cudaStream_t s);

@@ -37,6 +37,8 @@
 
 #pragma once
 
+#include <type_traits>
+
 #include "cafs_device.cuh"
 #include "cafs_internal.h"
 
@@ -324,7 +326,6 @@ struct Ring {
   template <typename F, class S>
   __device__ bool run(const Params& p, const K* keys, const unsigned* skip, F& f, const S& sc) {
     using T = KeyTraits<K>;
-    constexpr int VPE = T::kVec;
     constexpr int kConsumers = kConsumerWarps * 32;
     Ctrl* c = p.ctrl;
     const unsigned long long n = p.n;
@@ -349,18 +350,20 @@ struct Ring {
         }
       }
     } else {
+      // The skip flag is read one chunk ahead, so that its L2 latency
+      // overlaps the counting of the current chunk.
+      unsigned sk_next = (skip && lane == 0) ? ld_relaxed_u32(skip) : 0u;
       for (unsigned long long ch = 0; ch < nchunks; ++ch) {
         const int s = (int)(ch % kRingStages);
         const unsigned k = (unsigned)(ch / kRingStages);
+        const unsigned sk = __shfl_sync(0xffffffffu, sk_next, 0);
+        if (skip && lane == 0) sk_next = ld_relaxed_u32(skip);
         if (!mbar_wait(full + s, k & 1u, p.timeout_ns, c)) { ok = false; break; }
-        unsigned sk = 0;
-        if (lane == 0) sk = skip ? ld_relaxed_u32(skip) : 0u;
-        sk = __shfl_sync(0xffffffffu, sk, 0);
         if (!sk) {
-          const unsigned nk = bytes_of(ch) / (unsigned)sizeof(K);
-          const K* ck = reinterpret_cast<const K*>(buf + (size_t)s * kChunkBytes);
-          constexpr int KPT = kVecsPerThread * VPE;
-          f.template chunk<KPT, kConsumers>(ck + ctid, nk > (unsigned)ctid ? (nk - ctid + kConsumers - 1) / kConsumers : 0u);
+          const unsigned nv = bytes_of(ch) / 16u;
+          const typename T::Vec* cv = reinterpret_cast<const typename T::Vec*>(buf + (size_t)s * kChunkBytes);
+          f.template chunk<kVecsPerThread, kConsumers>(
+              cv + ctid, nv > (unsigned)ctid ? (nv - ctid + kConsumers - 1) / kConsumers : 0u);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
@@ -494,7 +497,7 @@ struct LocalTable {
   GlobalTable gt;
 
   __device__ __forceinline__ unsigned home(K x) const {
-    return (unsigned)hash_slot((unsigned long long)(typename KeyTraits<K>::U)x, logNB);
+    return local_bucket(fold32((typename KeyTraits<K>::U)x), logNB);
   }
   __device__ __forceinline__ void add(unsigned slot) const {
     atomicAdd(cnt + slot * R + lane_rep, 1u);
@@ -612,18 +615,27 @@ struct KeyCounter {
     if (!fast(x)) slow_insert<K>(x, lt, 1u);
   }
 
-  // Keys src[0], src[STRIDE], ..., src[(cnt-1)*STRIDE] (cnt <= B) of a chunk
-  // in shared memory.
-  template <int B, int STRIDE>
-  __device__ __forceinline__ void chunk(const K* src, unsigned cnt) {
+  // The 16-byte vectors src[0], src[STRIDE], ..., src[(cnt-1)*STRIDE]
+  // (cnt <= NV) of a chunk in shared memory, one vector load each.
+  template <int NV, int STRIDE>
+  __device__ __forceinline__ void chunk(const typename T::Vec* src, unsigned cnt) {
+    constexpr int VPE = T::kVec;
+    static_assert(NV * VPE <= 32, "miss mask");
     unsigned miss = 0;
     #pragma unroll
-    for (int i = 0; i < B; ++i)
-      if ((unsigned)i < cnt && !fast(src[i * STRIDE])) miss |= 1u << i;
+    for (int i = 0; i < NV; ++i) {
+      if ((unsigned)i < cnt) {
+        K e[VPE];
+        unpack(src[i * STRIDE], e);
+        #pragma unroll
+        for (int q = 0; q < VPE; ++q)
+          if (!fast(e[q])) miss |= 1u << (i * VPE + q);
+      }
+    }
     while (miss) {
       const int i = __ffs(miss) - 1;
       miss &= miss - 1;
-      slow_insert<K>(src[i * STRIDE], lt, 1u);
+      slow_insert<K>(reinterpret_cast<const K*>(src + (i / VPE) * STRIDE)[i % VPE], lt, 1u);
     }
   }
 };
@@ -882,6 +894,15 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
   unsigned* scan_part = scratch + kWarps;     // kThreads
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  if constexpr (std::is_same<S, CtaScope>::value) {
+    // One CTA owns the whole range: the digit starts are the exclusive scan
+    // of the pass histogram (counted for all passes up front), so the
+    // per-pass count read and the cross-CTA scan are not needed.
+    const unsigned v = threadIdx.x < kRadixDigits ? c->hist[pass][threadIdx.x] : 0u;
+    unsigned tot;
+    const unsigned ex = block_exclusive_scan(v, scratch, &tot);
+    if (threadIdx.x < kRadixDigits) running[threadIdx.x] = ex;
+  } else {
   // (a) digit counts of this CTA's range
   if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = 0u;
   __syncthreads();
@@ -923,8 +944,10 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
   }
   if (!sc.sync(c, epoch, p.timeout_ns)) return false;
 
-  // (c) rank and scatter this CTA's tiles in order
   if (threadIdx.x < kRadixDigits) running[threadIdx.x] = __ldcg(cta_base + b * kRadixDigits + threadIdx.x);
+  }
+
+  // (c) rank and scatter this CTA's tiles in order
   for (unsigned long long tile = tile0; tile < tile1; ++tile) {
     __syncthreads();
     const unsigned long long base = tile * kRadixTile;
@@ -1270,6 +1293,8 @@ enum ColumnEnd : int {
   kColumnDone = 0,     // output written
   kColumnRadix = 1,    // the path ends in the LSD radix fallback, not yet run
   kColumnFailed = 2,   // a bounded wait gave up; the status is in the record
+  kColumnTooBig = 3,   // the Eq. 6 table exceeds this workspace's table; nothing
+                       // was counted (only the sampler's record was written)
 };
 
 // Algorithm 3 for one column of n >= 2048 keys, run by the CTAs of `sc`:
@@ -1320,6 +1345,10 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
     ring.drain(p);
     if (sc.lead()) r.path = 5;  // HIGH_ENTROPY_RADIX
     return kColumnRadix;
+  }
+  if (r.C > p.table_cap) {   // only a capped batch workspace can be too small
+    ring.drain(p);
+    return kColumnTooBig;
   }
   if (d == 3) phase_count<K, true>(p, keys, smem, ring, sc);
   else phase_count<K, false>(p, keys, smem, ring, sc);

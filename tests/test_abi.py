@@ -86,7 +86,8 @@ def test_batch_argument_errors_are_synchronous(lib):
     cols[1].out = p + 128
     # bad knobs
     for bad in ({"local_slots_max": 300}, {"local_slots_max": 16384}, {"replicas_max": 3},
-                {"emit_tile_vec": 1000}, {"emit_tile_vec": 16384}, {"grid_min_n": 100}):
+                {"emit_tile_vec": 1000}, {"emit_tile_vec": 16384}, {"grid_min_n": 100},
+                {"cta_table_slots": 1000}, {"cta_table_slots": 32}):
         t = cafs.BatchTuning.from_dict(bad)
         assert lib.cafs_sort_batch_tuned(cols, 2, ctypes.byref(t), None, None) == 1, bad
         h = ctypes.c_void_p()
@@ -100,7 +101,47 @@ def test_batch_tuning_defaults(lib):
     t = cafs.BatchTuning()
     assert lib.cafs_batch_tuning_default(ctypes.byref(t)) == 0
     d = t.as_dict()
-    assert d == {"grid_min_n": 1 << 21, "defer_min_n": 1 << 15, "local_slots_max": 8192,
+    assert d == {"grid_min_n": 1 << 21, "defer_min_n": 0, "cta_table_slots": 0, "local_slots_max": 8192,
                  "replicas_max": 32, "emit_tile_vec": 4096, "ctas": 0}
     with pytest.raises(KeyError):
         cafs.BatchTuning.from_dict({"block": 3})
+
+
+def test_server_config_errors_are_synchronous(lib):
+    c = cafs.ServerConfig()
+    assert lib.cafs_server_config_default(ctypes.byref(c)) == 0
+    assert c.max_batch_columns == 1024 and c.max_inflight == 3 and c.max_request_keys == 1 << 22
+    assert c.tuning.cta_table_slots == 1 << 18 and c.tuning.grid_min_n == 1 << 23
+    h = ctypes.c_void_p()
+    bad = cafs.ServerConfig.from_buffer_copy(c)
+    bad.max_batch_columns = 0
+    assert lib.cafs_server_create(1 << 30, ctypes.byref(bad), ctypes.byref(h)) == 1
+    bad = cafs.ServerConfig.from_buffer_copy(c)
+    bad.reserved = 1
+    assert lib.cafs_server_create(1 << 30, ctypes.byref(bad), ctypes.byref(h)) == 1
+    bad = cafs.ServerConfig.from_buffer_copy(c)
+    bad.tuning.replicas_max = 5
+    assert lib.cafs_server_create(1 << 30, ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert not h.value
+    req = (cafs.Request * 2)()
+    arr = (ctypes.c_double * 2)(0.0, -1.0)
+    lat = (ctypes.c_double * 2)()
+    assert lib.cafs_serial_run_trace(req, 2, arr, lat, None, None, None) == 1   # negative arrival
+
+
+def test_autotune_argument_errors(lib):
+    cols = (cafs.Column * 1)()
+    ms = (ctypes.c_double * 2)()
+    best = ctypes.c_size_t()
+    cand = (cafs.BatchTuning * 2)()
+    assert lib.cafs_batch_autotune(cols, 0, cand, 0, 1, ms, ctypes.byref(best), None) == 1
+    assert lib.cafs_batch_autotune(cols, 0, cand, 2, 0, ms, ctypes.byref(best), None) == 1
+    cand[1].replicas_max = 3
+    assert lib.cafs_batch_autotune(cols, 0, cand, 2, 1, ms, ctypes.byref(best), None) == 1
+
+
+def test_workload_signature():
+    torch = pytest.importorskip("torch")
+    from paper_2605_25040_gb300 import autotune
+    keys = [torch.zeros(1000, dtype=torch.int64), torch.zeros(70000, dtype=torch.int32)]
+    assert autotune.workload_signature(keys) == "cols=2:i32=1:log2n=[9,16]:log2sum=16"

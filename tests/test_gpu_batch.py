@@ -116,6 +116,8 @@ def test_batch_set_aside_radix_columns():
 
 
 @pytest.mark.parametrize("tuning", [
+    {"cta_table_slots": 64},
+    {"cta_table_slots": 4096, "defer_min_n": 1 << 30},
     {"local_slots_max": 256, "replicas_max": 1},
     {"local_slots_max": 2048, "replicas_max": 4, "emit_tile_vec": 1024},
     {"emit_tile_vec": 8192, "ctas": 7},
@@ -181,3 +183,21 @@ def test_batch_launch_count_is_one():
     cafs.sort_batch(keys)
     torch.cuda.synchronize()
     assert cafs.kernel_launch_count() - before == 1
+
+
+def test_autotuner_times_candidates_and_caches(tmp_path):
+    from paper_2605_25040_gb300 import autotune
+    cols = mixed_small_columns(17)
+    keys = [torch.from_numpy(x).cuda() for x in cols]
+    outs = [torch.empty_like(k) for k in keys]
+    ms = cafs.time_tunings(keys, outs, [{}, {"emit_tile_vec": 1024}, {"local_slots_max": 2048}], reps=2)
+    assert len(ms) == 3 and all(m > 0 for m in ms)
+    for x, o in zip(cols, outs):        # the tuner's launches sorted the columns too
+        assert np.array_equal(o.cpu().numpy(), O.frequency_sort(x))
+    cache = str(tmp_path / "tune.json")
+    small = {"emit_tile_vec": [2048, 4096], "replicas_max": [8, 32]}
+    r1 = autotune.tuned(keys, outs, cache_path=cache, reps=1, rounds=1, space=small)
+    assert not r1["cached"] and r1["ms"] > 0 and r1["trials"] == 5
+    r2 = autotune.tuned(keys, outs, cache_path=cache, space=small)
+    assert r2["cached"] and r2["tuning"] == r1["tuning"]
+    run_batch(cols, tuning=r1["tuning"])
