@@ -12,9 +12,20 @@ region; each column (240 MB) is larger than L2, so no flush is needed.
 Printed JSON line (rank 0): value = whole-job Gkeys/s; roofline = the
 pipeline kernel's achieved bytes (one read + one write of every column, the
 sort's minimum traffic) per CUDA-event second against the measured HBM copy
-bandwidth; e2e = the same metric through cafs_sort_host with pinned host
-buffers (copies inside the timed region); cpu_baseline = the CPU oracle on a
-bounded sample of the same columns.
+bandwidth, with the DRAM traffic of the committed ncu summary when it was
+taken on the current kernel sources; e2e = the same metric through
+cafs_sort_host with pinned host buffers (copies inside the timed region);
+cpu_baseline = the CPU oracle on a bounded sample of the same columns.
+
+Two more legs (rank 0; --no-batched / --no-served skip them):
+  batched: 4096 int64 columns (N log-uniform [1e3, 1e6], K log-uniform
+    [2, min(N/4, 5e4)], Zipf 1.1) and 64 mixed int32/int64 columns (N 1e3..3e7,
+    K 2..N, 4 spill-trigger columns): one recorded batched launch (default
+    and autotuned knobs) against one cafs_sort per column;
+  served: open-loop Poisson traces at 1e3, 1e4, 1e5 requests/s (int64, N
+    log-uniform [1e3, 3e6], K log-uniform [2, 1e5], Zipf 1.1) against the
+    request server with an 8 GB budget and against serial cafs_sort_host;
+    p50/p99 latency and keys/s.
 
 ``--impl reference`` times the CPU oracle instead (the only "reference" this
 method has: the paper ships no code), on the same metric and columns.
@@ -151,19 +162,20 @@ class ClockSampler:
 
 
 def cpu_baseline(columns, budget_s: float = 12.0) -> dict:
-    """The CPU oracle (frequency_sort) as it stands on a bounded sample."""
+    """The CPU oracle (frequency_sort) as it stands on a bounded sample: the
+    given columns in turn, repeated until about ``budget_s`` of CPU work."""
     from oracle import cafs_oracle as O
-    keys, t, used = 0, 0.0, []
-    for name, x in columns:
+    keys, t, runs = 0, 0.0, 0
+    while t < budget_s:
+        name, x = columns[runs % len(columns)]
         t0 = time.perf_counter()
         O.frequency_sort(x)
         t += time.perf_counter() - t0
         keys += x.size
-        used.append(name)
-        if t > budget_s:
-            break
+        runs += 1
+    names = ", ".join(n for n, _ in columns)
     return {"value": keys / t / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(used)} full N={columns[0][1].size} sweep columns ({', '.join(used)}), "
+            "sample": f"{runs} sorts of N={columns[0][1].size} sweep columns taken in turn from ({names}), "
                       f"{t:.1f} s of numpy count-then-emit (single-threaded)"}
 
 

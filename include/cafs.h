@@ -176,7 +176,8 @@ typedef struct {
 /* Scheduling knobs of the batched kernel.  They change the speed, never a
  * result.  0 in any field selects the default (cafs_batch_tuning_default). */
 typedef struct {
-  uint64_t grid_min_n;      /* all-CTA columns: n >= this (>= 2048; 2^21)  */
+  uint64_t grid_min_n;      /* all-CTA columns: n >= this (>= 2048; 0: per
+                               batch, max(2^16, 2 * total keys / CTAs))    */
   uint64_t defer_min_n;     /* set-aside radix columns: n >= this (0: per
                                batch, max(2^15, queue keys / (2 * CTAs)))   */
   uint64_t cta_table_slots; /* hash table of each per-CTA slot, slots: power

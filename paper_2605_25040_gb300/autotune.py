@@ -28,7 +28,7 @@ SPACE = {
     "emit_tile_vec": [1024, 2048, 4096, 8192],
     "local_slots_max": [2048, 4096, 8192],
     "replicas_max": [8, 16, 32],
-    "grid_min_n": [1 << 19, 1 << 20, 1 << 21, 1 << 22],
+    "grid_min_n": [0, 1 << 19, 1 << 20, 1 << 21, 1 << 22],
     "defer_min_n": [0, 1 << 16, 1 << 18, 1 << 20],
 }
 

@@ -302,8 +302,10 @@ cafs_status tuning_from(const cafs_batch_tuning* t, Tuning* out) {
   Tuning d;
   if (t) {
     if (t->reserved != 0) return CAFS_ERR_INVALID_ARGUMENT;
-    if (t->grid_min_n) d.grid_min_n = t->grid_min_n;
-    if (d.grid_min_n < kSmallN) return CAFS_ERR_INVALID_ARGUMENT;
+    if (t->grid_min_n) {
+      if (t->grid_min_n < kSmallN) return CAFS_ERR_INVALID_ARGUMENT;
+      d.grid_min_n = t->grid_min_n;
+    }
     if (t->defer_min_n) d.defer_min_n = t->defer_min_n;
     if (t->cta_table_slots) {
       const unsigned long long v = t->cta_table_slots;
@@ -385,7 +387,12 @@ cafs_status batch_grid(int dev, int* grid) {
 }
 
 
-cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t, Schedule* s) {
+unsigned long long resolve_grid_min(const Tuning& t, unsigned long long total_keys, int grid) {
+  if (t.grid_min_n) return t.grid_min_n;
+  return std::max(1ull << 16, 2ull * total_keys / (unsigned long long)(grid > 0 ? grid : 1));
+}
+
+cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t, int grid, Schedule* s) {
   s->cols.clear();
   s->grid_items.clear();
   s->cta_items.clear();
@@ -393,11 +400,17 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
   if (ncols && !cols) return CAFS_ERR_INVALID_ARGUMENT;
   if (ncols > 0xFFFFFFF0ull) return CAFS_ERR_TOO_LARGE;
   s->cols.resize(ncols);
+  unsigned long long total = 0;
   for (size_t i = 0; i < ncols; ++i) {
     const cafs_column& c = cols[i];
     if (c.reserved != 0) return CAFS_ERR_INVALID_ARGUMENT;
     cafs_status st = check_args(c.keys, c.n, c.dtype, c.out, true);
     if (st != CAFS_OK) return st;
+    total += c.n;
+  }
+  const unsigned long long grid_min = resolve_grid_min(t, total, grid);
+  for (size_t i = 0; i < ncols; ++i) {
+    const cafs_column& c = cols[i];
     BatchColumn& b = s->cols[i];
     b.keys = c.keys;
     b.out = c.out;
@@ -405,7 +418,7 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
     b.dtype = c.dtype == CAFS_INT64 ? 1 : 0;
     b.pad = 0;
     if (c.n == 0) continue;
-    if ((unsigned long long)c.n >= t.grid_min_n) {
+    if ((unsigned long long)c.n >= grid_min) {
       s->grid_items.push_back((unsigned)i);
       s->n_max_grid = std::max(s->n_max_grid, (unsigned long long)c.n);
     } else {
@@ -612,7 +625,8 @@ cafs_status cafs_sort_batch_tuned(const cafs_column* cols, size_t ncols, const c
   cafs_status st = tuning_from(tuning, &t);
   if (st != CAFS_OK) return st;
   Schedule sc;
-  if ((st = make_schedule(cols, ncols, t, &sc)) != CAFS_OK) return st;
+  // Argument errors first, before any CUDA call; then the real schedule.
+  if ((st = make_schedule(cols, ncols, t, 1, &sc)) != CAFS_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lock(g_batch_mu);
   int dev = 0;
@@ -621,6 +635,7 @@ cafs_status cafs_sort_batch_tuned(const cafs_column* cols, size_t ncols, const c
   if ((st = batch_device(dev, &d)) != CAFS_OK) return st;
   int grid = d->grid;
   if (t.ctas && (int)t.ctas < grid) grid = (int)t.ctas;
+  if ((st = make_schedule(cols, ncols, t, grid, &sc)) != CAFS_OK) return st;
   auto key = std::make_pair(dev, reinterpret_cast<uintptr_t>(s));
   BatchBuffers*& b = g_batch_ws[key];
   if (!b) {
@@ -645,7 +660,7 @@ cafs_status cafs_batch_plan_create(const cafs_column* cols, size_t ncols, const 
   *out = nullptr;
   cafs_batch_plan* pl = new cafs_batch_plan();
   cafs_status st = tuning_from(tuning, &pl->tuning);
-  if (st == CAFS_OK) st = make_schedule(cols, ncols, pl->tuning, &pl->sched);
+  if (st == CAFS_OK) st = make_schedule(cols, ncols, pl->tuning, 1, &pl->sched);
   if (st != CAFS_OK) {
     delete pl;
     return st;
@@ -665,6 +680,7 @@ cafs_status cafs_batch_plan_create(const cafs_column* cols, size_t ncols, const 
   int grid = 0;
   if ((st = batch_grid(dev, &grid)) != CAFS_OK) return fail(st);
   if (pl->tuning.ctas && (int)pl->tuning.ctas < grid) grid = (int)pl->tuning.ctas;
+  if ((st = make_schedule(cols, ncols, pl->tuning, grid, &pl->sched)) != CAFS_OK) return fail(st);
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(CAFS_ERR_CUDA);
   if ((st = ensure_batch(&pl->buf, grid, pl->sched, pl->tuning, s)) != CAFS_OK) return fail(st);
   if ((st = upload(&pl->buf, pl->sched, s)) != CAFS_OK) return fail(st);

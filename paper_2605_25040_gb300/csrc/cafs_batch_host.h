@@ -13,7 +13,7 @@
 namespace cafs {
 
 struct Tuning {
-  unsigned long long grid_min_n = 1ull << 21;
+  unsigned long long grid_min_n = 0;        // 0: resolved per batch by make_schedule
   unsigned long long defer_min_n = 0;       // 0: resolve_defer() picks it per batch
   unsigned long long cta_table_slots = 0;   // 0: what the longest queue column can need
   unsigned local_slots_max = kLocalSlotsMax;
@@ -59,8 +59,11 @@ struct Schedule {
 cafs_status tuning_from(const cafs_batch_tuning* t, Tuning* out);
 void tuning_to(const Tuning& d, cafs_batch_tuning* t);
 // Validates the columns and orders the work: all-CTA columns, then the
-// queue, longest first.
-cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t, Schedule* s);
+// queue, longest first.  With grid_min_n 0 a column goes to the all-CTA
+// stage when one CTA would take more than twice the batch's average work
+// per CTA to sort it: n >= max(2^16, 2 * total keys / grid).
+cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t, int grid, Schedule* s);
+unsigned long long resolve_grid_min(const Tuning& t, unsigned long long total_keys, int grid);
 // The set-aside threshold of a batch: the knob, or (knob 0) the length at
 // which one CTA's radix sort of a column (about 17 passes over its keys)
 // would take longer than about twice the queue's average work per CTA.

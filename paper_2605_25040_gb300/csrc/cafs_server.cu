@@ -188,7 +188,7 @@ void scheduler_loop(cafs_server* sv) {
     if (st == CAFS_OK && (cudaEventRecord(sv->ev_in, sv->s_in) != cudaSuccess ||
                           cudaStreamWaitEvent(sv->s_run, sv->ev_in, 0) != cudaSuccess))
       st = CAFS_ERR_CUDA;
-    if (st == CAFS_OK) st = make_schedule(cols.data(), cols.size(), sv->tuning, &sc);
+    if (st == CAFS_OK) st = make_schedule(cols.data(), cols.size(), sv->tuning, sv->grid, &sc);
     if (st == CAFS_OK) st = upload(&sv->buf, sc, sv->s_run);
     if (st == CAFS_OK) {
       const BatchParams bp = make_params(&sv->buf, sc, sv->tuning);
@@ -302,7 +302,6 @@ cafs_status cafs_server_config_default(cafs_server_config* cfg) {
   cfg->max_inflight = 3;
   cfg->max_request_keys = 1ull << 22;
   Tuning t;
-  t.grid_min_n = 1ull << 23;        // every admissible request goes to the queue
   t.cta_table_slots = 1ull << 18;   // larger Eq. 6 tables are set aside
   t.defer_min_n = 1ull << 16;       // fixed, so the per-CTA radix buffers stay small
   tuning_to(t, &cfg->tuning);
@@ -349,8 +348,9 @@ cafs_status cafs_server_create(size_t mem_budget_bytes, const cafs_server_config
   Schedule worst;
   worst.cols.resize(sv->max_batch);
   const unsigned long long nmax = sv->max_request_keys;
-  if (nmax >= sv->tuning.grid_min_n) worst.n_max_grid = nmax;
-  worst.n_max_cta = std::min(nmax, sv->tuning.grid_min_n - 1);
+  const unsigned long long gmin = sv->tuning.grid_min_n ? sv->tuning.grid_min_n : nmax + 1;
+  if (nmax >= gmin) worst.n_max_grid = nmax;
+  worst.n_max_cta = std::min(nmax, gmin - 1);
   if ((st = ensure_batch(&sv->buf, sv->grid, worst, sv->tuning, sv->s_run)) != CAFS_OK) return fail(st);
   if (cudaStreamSynchronize(sv->s_run) != cudaSuccess) return fail(CAFS_ERR_CUDA);
   size_t free_b = 0, total_b = 0;

@@ -101,7 +101,7 @@ def test_batch_tuning_defaults(lib):
     t = cafs.BatchTuning()
     assert lib.cafs_batch_tuning_default(ctypes.byref(t)) == 0
     d = t.as_dict()
-    assert d == {"grid_min_n": 1 << 21, "defer_min_n": 0, "cta_table_slots": 0, "local_slots_max": 8192,
+    assert d == {"grid_min_n": 0, "defer_min_n": 0, "cta_table_slots": 0, "local_slots_max": 8192,
                  "replicas_max": 32, "emit_tile_vec": 4096, "ctas": 0}
     with pytest.raises(KeyError):
         cafs.BatchTuning.from_dict({"block": 3})
@@ -111,7 +111,7 @@ def test_server_config_errors_are_synchronous(lib):
     c = cafs.ServerConfig()
     assert lib.cafs_server_config_default(ctypes.byref(c)) == 0
     assert c.max_batch_columns == 1024 and c.max_inflight == 3 and c.max_request_keys == 1 << 22
-    assert c.tuning.cta_table_slots == 1 << 18 and c.tuning.grid_min_n == 1 << 23
+    assert c.tuning.cta_table_slots == 1 << 18 and c.tuning.grid_min_n == 0
     h = ctypes.c_void_p()
     bad = cafs.ServerConfig.from_buffer_copy(c)
     bad.max_batch_columns = 0
