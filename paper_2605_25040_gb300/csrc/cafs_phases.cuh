@@ -252,6 +252,7 @@ struct Ring {
   unsigned char* buf;           // kRingBytes
   unsigned long long* full;     // kRingStages
   unsigned long long* empty;    // kRingStages
+  unsigned* skip_flag;          // shared copy of the caller's skip flag
   const unsigned char* src;     // first byte of this CTA's vector range
   unsigned long long total;     // bytes of this CTA's vector range
   unsigned long long nchunks;
@@ -268,6 +269,8 @@ struct Ring {
     buf = smem + (kPipelineSmem - kRingBytes);
     full = reinterpret_cast<unsigned long long*>(buf - 128);
     empty = full + kRingStages;
+    skip_flag = reinterpret_cast<unsigned*>(empty + kRingStages);
+    static_assert(2 * kRingStages * 8 + 4 <= 128, "ring barriers and flag below the ring");
     src = reinterpret_cast<const unsigned char*>(keys + sh.head) + sh.v0 * 16ull;
     total = (sh.v1 - sh.v0) * 16ull;
     nchunks = (total + kChunkBytes - 1) / kChunkBytes;
@@ -279,6 +282,7 @@ struct Ring {
         mbar_init(empty + s, kConsumerWarps);
       }
       fence_mbar_init();
+      *skip_flag = 0u;
     }
     // The ring's bytes may hold an earlier phase's (or column's) generic
     // stores: every thread fences them against the coming bulk copies.
@@ -342,23 +346,28 @@ struct Ring {
     bool ok = true;
     if (!consumer) {
       if (producer()) {
+        // The producer mirrors the (global) skip flag into shared memory,
+        // one chunk late: its L2 read overlaps the wait for a free stage,
+        // and the consumers only read shared memory (a global read per
+        // chunk and warp cost 13 us of a 70 us count phase).
+        unsigned fl = skip ? ld_relaxed_u32(skip) : 0u;
         for (; issued < nchunks; ++issued) {
           const int s = (int)(issued % kRingStages);
           const unsigned k = (unsigned)(issued / kRingStages);
           if (!mbar_wait(empty + s, (k - 1) & 1u, p.timeout_ns, c)) { ok = false; break; }
+          if (skip) {
+            *reinterpret_cast<volatile unsigned*>(skip_flag) = fl;
+            fl = ld_relaxed_u32(skip);
+          }
           issue(issued);
         }
       }
     } else {
-      // The skip flag is read one chunk ahead, so that its L2 latency
-      // overlaps the counting of the current chunk.
-      unsigned sk_next = (skip && lane == 0) ? ld_relaxed_u32(skip) : 0u;
       for (unsigned long long ch = 0; ch < nchunks; ++ch) {
         const int s = (int)(ch % kRingStages);
         const unsigned k = (unsigned)(ch / kRingStages);
-        const unsigned sk = __shfl_sync(0xffffffffu, sk_next, 0);
-        if (skip && lane == 0) sk_next = ld_relaxed_u32(skip);
         if (!mbar_wait(full + s, k & 1u, p.timeout_ns, c)) { ok = false; break; }
+        const unsigned sk = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile unsigned*>(skip_flag), 0);
         if (!sk) {
           const unsigned nv = bytes_of(ch) / 16u;
           const typename T::Vec* cv = reinterpret_cast<const typename T::Vec*>(buf + (size_t)s * kChunkBytes);
@@ -783,10 +792,14 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     return res;
   }();
 
-  // Flush the shared table into the global table.
+  // Flush the shared table into the global table.  CTAs hold mostly the
+  // same keys in the same local slots; each starts at its own offset so
+  // that they do not all add to the same global slot at the same time.
   if (use_local) {
     const GlobalTable g = global_table(p);
-    for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    const int rot = (int)((sc.part() * 977u) & (unsigned)(S - 1));
+    for (int i0 = threadIdx.x; i0 < S; i0 += blockDim.x) {
+      const int i = (i0 + rot) & (S - 1);
       const K k = lkeys[i];
       if (k != kmin) {
         unsigned tot = 0;
