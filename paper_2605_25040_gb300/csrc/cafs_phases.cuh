@@ -604,31 +604,28 @@ struct KeyCounter {
       return true;
     }
     if (!TINY && lt.keys) {
+      // Slots of a bucket fill in order and a key sits in the first bucket
+      // (from its home on) that had a free slot when it came, so a bucket
+      // whose last slot is still free ends the search.  Up to kFastBuckets
+      // buckets are searched here; the rest (about 1 % of the keys at the
+      // largest load, 1/2) go to the slow path.
       constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
-      const unsigned b = lt.home(x);
-      K k[kBucketSlots];
-      load_bucket(lt.keys + b * kBucketSlots, k);
-      int hit = -1;
+      constexpr int kFastBuckets = 3;
+      unsigned b = lt.home(x);
       #pragma unroll
-      for (int j = kBucketSlots - 1; j >= 0; --j)
-        if (k[j] == x) hit = j;
-      if (hit >= 0) {
-        lt.add(b * kBucketSlots + hit);
-        return true;
-      }
-      // Slots of a bucket fill in order, so a full home bucket (last slot
-      // taken) is the only case where the key can sit further on: look in
-      // the next bucket too before taking the slow path.
-      if (k[kBucketSlots - 1] != T::min_key()) {
-        const unsigned b2 = (b + 1) & (unsigned)(lt.NB - 1);
-        load_bucket(lt.keys + b2 * kBucketSlots, k);
+      for (int probe = 0; probe < kFastBuckets; ++probe) {
+        K k[kBucketSlots];
+        load_bucket(lt.keys + b * kBucketSlots, k);
+        int hit = -1;
         #pragma unroll
         for (int j = kBucketSlots - 1; j >= 0; --j)
           if (k[j] == x) hit = j;
         if (hit >= 0) {
-          lt.add(b2 * kBucketSlots + hit);
+          lt.add(b * kBucketSlots + hit);
           return true;
         }
+        if (k[kBucketSlots - 1] == T::min_key()) break;
+        b = (b + 1) & (unsigned)(lt.NB - 1);
       }
     }
     return false;
@@ -1322,6 +1319,15 @@ __device__ __forceinline__ void mark(Ctrl* c, int i, const S& sc) {
   if (sc.lead()) c->rec.timeline[i] = global_timer_ns();
 }
 
+// Head start of the sampling CTA's loads over the other CTAs' ring (ns).
+constexpr unsigned long long kSampleHeadStartNs = 2500;
+
+// Waits about `ns` nanoseconds (global timer).
+__device__ __forceinline__ void spin_ns(unsigned long long ns) {
+  const unsigned long long t0 = global_timer_ns();
+  while (global_timer_ns() - t0 < ns) __nanosleep(200);
+}
+
 // How a column's pass through column_body() ended.
 enum ColumnEnd : int {
   kColumnDone = 0,     // output written
@@ -1345,11 +1351,21 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
   K* out = reinterpret_cast<K*>(p.out);
 
   // The count phase's first chunks are on their way while part 0 samples.
+  // With the whole grid on one column, the sampling CTA's 1024 strided
+  // loads go first: it starts its own ring after sampling, and the other
+  // CTAs start theirs after a short head start (their first chunks still
+  // land long before counting begins; queued behind them, the samples took
+  // about 8 us instead of 2).
+  constexpr bool kGrid = std::is_same<S, GridScope>::value;
+  const bool sampler = sc.part() == 0;
   Ring<K> ring;
-  if (p.mode == kModeSort) ring.start(p, keys, smem, sc);
-  else ring.live = false;
-
-  if (sc.part() == 0) phase_sample<K>(p, keys, smem);
+  ring.live = false;
+  if (p.mode == kModeSort && !(kGrid && sampler)) {
+    if (kGrid) spin_ns(kSampleHeadStartNs);
+    ring.start(p, keys, smem, sc);
+  }
+  if (sampler) phase_sample<K>(p, keys, smem);
+  if (kGrid && sampler && p.mode == kModeSort) ring.start(p, keys, smem, sc);
   if (!sc.sync(c, epoch, p.timeout_ns)) { ring.drain(p); return kColumnFailed; }
   mark(c, 1, sc);
 

@@ -200,3 +200,14 @@ def test_bounded_wait_reports_timeout():
         cafs.set_test_hooks(0, 0)
     # the context is still usable
     check_sort(x)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_emit_tiles_with_a_few_short_runs(dtype, offset):
+    # Output runs 50000, 1, 2, 3, 49994 (and variants): one emit tile holds
+    # several boundaries, some inside one 16-byte vector.
+    for lens in ([50_000, 1, 2, 3, 49_994], [49_999, 1, 1, 1, 1, 1, 1, 49_995],
+                 [16_381, 3, 16_000, 5, 7, 30_000]):
+        x = np.repeat(np.arange(len(lens), dtype=dtype) * 7 - 3, lens)
+        check_sort(G.shuffle(x, sum(lens)), offset=offset)
