@@ -895,6 +895,66 @@ __device__ __forceinline__ unsigned radix_digit(K k, int shift) {
 // counts (CTA b takes digits d = b, b + G, ...), with a grid barrier after
 // each step; (c) every CTA ranks each tile in shared memory (stable: a
 // per-warp match on the digit, warps in order) and writes it out.
+// Half-CTA pipelines of a radix pass: the CTA's range is cut into half-tiles
+// of kHalfTile keys, taken alternately by the two halves of the CTA (512
+// threads each, own shared memory, own named barrier).  A half-tile gets its
+// digit bases from the CTA's running cursor, which the halves hand to each
+// other in half-tile order through a turn counter, so every digit keeps the
+// input order (the pass is stable) while one half waits at its barriers and
+// the other ranks or writes.
+constexpr int kHalfThreads = kThreads / 2;
+constexpr int kHalfWarps = kHalfThreads / 32;
+constexpr int kHalfTile = kHalfThreads * kRadixItems;
+
+__device__ __forceinline__ void half_sync(int h) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(kHalfThreads) : "memory");
+}
+
+// Exclusive scan of one value per thread of a half (all its threads call it).
+__device__ __forceinline__ unsigned half_exclusive_scan(unsigned v, unsigned* scratch, int h) {
+  const int t = threadIdx.x - h * kHalfThreads, w = t >> 5, l = t & 31;
+  unsigned x = v;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (l >= o) x += y;
+  }
+  half_sync(h);
+  if (l == 31) scratch[w] = x;
+  half_sync(h);
+  if (w == 0) {
+    unsigned sw = (l < kHalfWarps) ? scratch[l] : 0u;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, sw, o);
+      if (l >= o) sw += y;
+    }
+    if (l < kHalfWarps) scratch[l] = sw;
+  }
+  half_sync(h);
+  return ((w > 0) ? scratch[w - 1] : 0u) + x - v;
+}
+
+template <typename K, bool PAY>
+struct HalfSmem {
+  K stage_k[kHalfTile];
+  unsigned stage_v[PAY ? kHalfTile : 1];
+  unsigned short wcnt[kHalfWarps * kRadixDigits];
+  unsigned tile_cnt[kRadixDigits];
+  unsigned tile_start[kRadixDigits];
+  unsigned base[kRadixDigits];
+  unsigned scratch[kHalfWarps];
+  unsigned scan_part[kHalfThreads];
+};
+
+struct PassSmem {
+  unsigned running[kRadixDigits];   // the CTA's digit cursor
+  unsigned hist[kRadixDigits];
+  unsigned scratch[kWarps];
+  unsigned turn;                    // next half-tile allowed to take bases
+  unsigned failed;
+};
+
 template <typename K, bool PAY, class S>
 __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v, K* out_k,
                            unsigned* out_v, unsigned long long n, int pass, unsigned char* smem,
@@ -904,20 +964,23 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
   const unsigned long long ntiles = (n + kRadixTile - 1) / kRadixTile;
   const unsigned b = sc.part(), nb = sc.nparts();
   const unsigned long long tile0 = ntiles * b / nb, tile1 = ntiles * (b + 1) / nb;
+  const unsigned long long i0 = tile0 * kRadixTile;
+  const unsigned long long i1 = tile1 * kRadixTile < n ? tile1 * kRadixTile : n;
   unsigned* cta_cnt = reinterpret_cast<unsigned*>(p.lookback);       // [nb][256]
   unsigned* cta_base = cta_cnt + nb * kRadixDigits;                   // [nb][256]
 
-  K* stage_k = reinterpret_cast<K*>(smem);
-  unsigned* stage_v = reinterpret_cast<unsigned*>(stage_k + kRadixTile);
-  unsigned short* wcnt = reinterpret_cast<unsigned short*>(stage_v + (PAY ? kRadixTile : 0));
-  unsigned* tile_cnt = reinterpret_cast<unsigned*>(wcnt + kWarps * kRadixDigits);
-  unsigned* tile_start = tile_cnt + kRadixDigits;
-  unsigned* running = tile_start + kRadixDigits;
-  unsigned* hist = running + kRadixDigits;
-  unsigned* scratch = hist + kRadixDigits;    // kWarps
-  unsigned* scan_part = scratch + kWarps;     // kThreads
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  PassSmem* ps = reinterpret_cast<PassSmem*>(smem);
+  constexpr size_t kPassBytes = (sizeof(PassSmem) + 127) & ~size_t(127);
+  constexpr size_t kHalfBytes = (sizeof(HalfSmem<K, PAY>) + 127) & ~size_t(127);
+  static_assert(kPassBytes + 2 * kHalfBytes <= (size_t)kPipelineSmem, "radix pass shared memory");
+  unsigned* running = ps->running;
+  unsigned* hist = ps->hist;
+  unsigned* scratch = ps->scratch;
 
+  if (threadIdx.x == 0) {
+    ps->turn = 0u;
+    ps->failed = 0u;
+  }
   if constexpr (std::is_same<S, CtaScope>::value) {
     // One CTA owns the whole range: the digit starts are the exclusive scan
     // of the pass histogram (counted for all passes up front), so the
@@ -927,55 +990,59 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     const unsigned ex = block_exclusive_scan(v, scratch, &tot);
     if (threadIdx.x < kRadixDigits) running[threadIdx.x] = ex;
   } else {
-  // (a) digit counts of this CTA's range
-  if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = 0u;
-  __syncthreads();
-  {
-    const unsigned long long i0 = tile0 * kRadixTile;
-    const unsigned long long i1 = tile1 * kRadixTile < n ? tile1 * kRadixTile : n;
-    constexpr int U = 4;
-    for (unsigned long long base = i0 + threadIdx.x; base < i1; base += (unsigned long long)U * kThreads) {
-      K kk[U];
-      #pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const unsigned long long i = base + (unsigned long long)j * kThreads;
-        kk[j] = i < i1 ? __ldcg(in_k + i) : (K)0;
-      }
-      #pragma unroll
-      for (int j = 0; j < U; ++j)
-        if (base + (unsigned long long)j * kThreads < i1) atomicAdd(hist + radix_digit(kk[j], shift), 1u);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < kRadixDigits) cta_cnt[b * kRadixDigits + threadIdx.x] = hist[threadIdx.x];
-  if (!sc.sync(c, epoch, p.timeout_ns)) return false;
-
-  // (b) exclusive scan over CTAs of each digit (this CTA's digits), offset
-  // by the digit's global start (exclusive scan of the pass histogram)
-  {
-    const unsigned v = threadIdx.x < kRadixDigits ? ld_relaxed_u32(&c->hist[pass][threadIdx.x]) : 0u;
-    unsigned tot;
-    const unsigned ex = block_exclusive_scan(v, scratch, &tot);
-    if (threadIdx.x < kRadixDigits) tile_start[threadIdx.x] = ex;   // digit starts (reused below)
-  }
-  __syncthreads();
-  for (int d = (int)b; d < kRadixDigits; d += (int)nb) {
-    const unsigned dstart = tile_start[d];
-    const unsigned v = threadIdx.x < nb ? __ldcg(cta_cnt + threadIdx.x * kRadixDigits + d) : 0u;
-    unsigned tot;
-    const unsigned ex = block_exclusive_scan(v, scratch, &tot);
-    if (threadIdx.x < nb) cta_base[threadIdx.x * kRadixDigits + d] = dstart + ex;
-  }
-  if (!sc.sync(c, epoch, p.timeout_ns)) return false;
-
-  if (threadIdx.x < kRadixDigits) running[threadIdx.x] = __ldcg(cta_base + b * kRadixDigits + threadIdx.x);
-  }
-
-  // (c) rank and scatter this CTA's tiles in order
-  for (unsigned long long tile = tile0; tile < tile1; ++tile) {
+    // (a) digit counts of this CTA's range
+    if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = 0u;
     __syncthreads();
-    const unsigned long long base = tile * kRadixTile;
-    for (int d = lane; d < kRadixDigits; d += 32) wcnt[w * kRadixDigits + d] = 0;
+    {
+      constexpr int U = 4;
+      for (unsigned long long base = i0 + threadIdx.x; base < i1; base += (unsigned long long)U * kThreads) {
+        K kk[U];
+        #pragma unroll
+        for (int j = 0; j < U; ++j) {
+          const unsigned long long i = base + (unsigned long long)j * kThreads;
+          kk[j] = i < i1 ? __ldcg(in_k + i) : (K)0;
+        }
+        #pragma unroll
+        for (int j = 0; j < U; ++j)
+          if (base + (unsigned long long)j * kThreads < i1) atomicAdd(hist + radix_digit(kk[j], shift), 1u);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kRadixDigits) cta_cnt[b * kRadixDigits + threadIdx.x] = hist[threadIdx.x];
+    if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+
+    // (b) exclusive scan over CTAs of each digit (this CTA's digits), offset
+    // by the digit's global start (exclusive scan of the pass histogram)
+    {
+      const unsigned v = threadIdx.x < kRadixDigits ? ld_relaxed_u32(&c->hist[pass][threadIdx.x]) : 0u;
+      unsigned tot;
+      const unsigned ex = block_exclusive_scan(v, scratch, &tot);
+      if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = ex;   // digit starts
+    }
+    __syncthreads();
+    for (int d = (int)b; d < kRadixDigits; d += (int)nb) {
+      const unsigned dstart = hist[d];
+      const unsigned v = threadIdx.x < nb ? __ldcg(cta_cnt + threadIdx.x * kRadixDigits + d) : 0u;
+      unsigned tot;
+      const unsigned ex = block_exclusive_scan(v, scratch, &tot);
+      if (threadIdx.x < nb) cta_base[threadIdx.x * kRadixDigits + d] = dstart + ex;
+    }
+    if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+    if (threadIdx.x < kRadixDigits) running[threadIdx.x] = __ldcg(cta_base + b * kRadixDigits + threadIdx.x);
+  }
+  __syncthreads();
+
+  // (c) rank and scatter the CTA's range in half-tiles
+  const int h = threadIdx.x / kHalfThreads;
+  const int t = threadIdx.x - h * kHalfThreads;
+  const int w = t >> 5, lane = t & 31;
+  HalfSmem<K, PAY>* hs = reinterpret_cast<HalfSmem<K, PAY>*>(smem + kPassBytes + (size_t)h * kHalfBytes);
+  const unsigned long long nhalf = (i1 - i0 + kHalfTile - 1) / kHalfTile;
+  for (unsigned long long q = (unsigned long long)h; q < nhalf; q += 2) {
+    const unsigned long long base = i0 + q * kHalfTile;
+    const unsigned cnt = (unsigned)((i1 - base) < (unsigned long long)kHalfTile ? (i1 - base) : kHalfTile);
+    half_sync(h);
+    for (int d = lane; d < kRadixDigits; d += 32) hs->wcnt[w * kRadixDigits + d] = 0;
     __syncwarp();
     K key[kRadixItems];
     unsigned rd[kRadixItems];   // rank within the warp << 16 | digit (256 = no item)
@@ -983,7 +1050,7 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     #pragma unroll
     for (int j = 0; j < kRadixItems; ++j) {
       const unsigned long long idx = wbase + j * 32;
-      const bool valid = idx < n;
+      const bool valid = idx < i1;
       key[j] = valid ? __ldcg(in_k + idx) : (K)0;
       rd[j] = valid ? radix_digit(key[j], shift) : (unsigned)kRadixDigits;
     }
@@ -994,77 +1061,95 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
       const int leader = __ffs(peers) - 1;
       unsigned old = 0;
       if (lane == leader && d < (unsigned)kRadixDigits) {
-        old = wcnt[w * kRadixDigits + d];
-        wcnt[w * kRadixDigits + d] = (unsigned short)(old + __popc(peers));
+        old = hs->wcnt[w * kRadixDigits + d];
+        hs->wcnt[w * kRadixDigits + d] = (unsigned short)(old + __popc(peers));
       }
       old = __shfl_sync(0xffffffffu, old, leader);
       __syncwarp();
       rd[j] = d | ((old + __popc(peers & lanemask_lt())) << 16);
     }
-    __syncthreads();
-    // Per digit: exclusive scan over warps and tile total.  kScanGroups
-    // threads per digit each scan a slice of the warps, then the slices'
-    // totals are combined.
+    half_sync(h);
+    // Per digit: exclusive scan over the half's warps and the half-tile total.
     {
-      constexpr int kScanGroups = kThreads / kRadixDigits;
-      constexpr int kWarpsPerGroup = kWarps / kScanGroups;
-      static_assert(kScanGroups * kRadixDigits == kThreads, "scan groups");
-      const int d = threadIdx.x % kRadixDigits, g = threadIdx.x / kRadixDigits;
+      constexpr int kScanGroups = kHalfThreads / kRadixDigits;
+      constexpr int kWarpsPerGroup = kHalfWarps / kScanGroups;
+      static_assert(kScanGroups * kRadixDigits == kHalfThreads, "scan groups");
+      const int d = t % kRadixDigits, g = t / kRadixDigits;
       unsigned run = 0;
       #pragma unroll
-      for (int q = g * kWarpsPerGroup; q < (g + 1) * kWarpsPerGroup; ++q) {
-        const unsigned x = wcnt[q * kRadixDigits + d];
-        wcnt[q * kRadixDigits + d] = (unsigned short)run;
+      for (int qq = g * kWarpsPerGroup; qq < (g + 1) * kWarpsPerGroup; ++qq) {
+        const unsigned x = hs->wcnt[qq * kRadixDigits + d];
+        hs->wcnt[qq * kRadixDigits + d] = (unsigned short)run;
         run += x;
       }
-      scan_part[g * kRadixDigits + d] = run;
-      __syncthreads();
+      hs->scan_part[g * kRadixDigits + d] = run;
+      half_sync(h);
       unsigned before = 0, tot = 0;
       #pragma unroll
-      for (int q = 0; q < kScanGroups; ++q) {
-        const unsigned v = scan_part[q * kRadixDigits + d];
-        before += q < g ? v : 0u;
+      for (int qq = 0; qq < kScanGroups; ++qq) {
+        const unsigned v = hs->scan_part[qq * kRadixDigits + d];
+        before += qq < g ? v : 0u;
         tot += v;
       }
       if (g > 0) {
         #pragma unroll
-        for (int q = g * kWarpsPerGroup; q < (g + 1) * kWarpsPerGroup; ++q)
-          wcnt[q * kRadixDigits + d] = (unsigned short)(wcnt[q * kRadixDigits + d] + before);
+        for (int qq = g * kWarpsPerGroup; qq < (g + 1) * kWarpsPerGroup; ++qq)
+          hs->wcnt[qq * kRadixDigits + d] = (unsigned short)(hs->wcnt[qq * kRadixDigits + d] + before);
       }
-      if (g == 0) tile_cnt[d] = tot;
+      if (g == 0) hs->tile_cnt[d] = tot;
     }
-    __syncthreads();
+    half_sync(h);
     {
-      const unsigned v = threadIdx.x < kRadixDigits ? tile_cnt[threadIdx.x] : 0u;
-      unsigned tot;
-      const unsigned ex = block_exclusive_scan(v, scratch, &tot);
-      if (threadIdx.x < kRadixDigits) tile_start[threadIdx.x] = ex;
+      const unsigned v = t < kRadixDigits ? hs->tile_cnt[t] : 0u;
+      const unsigned ex = half_exclusive_scan(v, hs->scratch, h);
+      if (t < kRadixDigits) hs->tile_start[t] = ex;
     }
-    __syncthreads();
-    // Scatter into shared memory in tile-sorted order.
+    // Take this half-tile's digit bases from the cursor, in half-tile order.
+    if (t == 0) {
+      const unsigned long long t0 = global_timer_ns();
+      unsigned it = 0;
+      while (*reinterpret_cast<volatile unsigned*>(&ps->turn) != (unsigned)q) {
+        if (*reinterpret_cast<volatile unsigned*>(&ps->failed)) break;
+        if ((++it & 255u) == 0 && global_timer_ns() - t0 > p.timeout_ns) {
+          atomicExch(&c->rec.status, kDevTimeout);
+          *reinterpret_cast<volatile unsigned*>(&ps->failed) = 1u;
+          break;
+        }
+      }
+      __threadfence_block();
+    }
+    half_sync(h);
+    if (*reinterpret_cast<volatile unsigned*>(&ps->failed)) break;
+    if (t < kRadixDigits) {
+      hs->base[t] = running[t];
+      running[t] += hs->tile_cnt[t];
+    }
+    half_sync(h);
+    if (t == 0) {
+      __threadfence_block();
+      *reinterpret_cast<volatile unsigned*>(&ps->turn) = (unsigned)q + 1u;
+    }
+    // Scatter into shared memory in half-tile-sorted order.
     #pragma unroll
     for (int j = 0; j < kRadixItems; ++j) {
       const unsigned d = rd[j] & 0xFFFFu;
       if (d < (unsigned)kRadixDigits) {
-        const unsigned pos = tile_start[d] + wcnt[w * kRadixDigits + d] + (rd[j] >> 16);
-        stage_k[pos] = key[j];
-        if constexpr (PAY) stage_v[pos] = __ldcg(in_v + wbase + j * 32);
+        const unsigned pos = hs->tile_start[d] + hs->wcnt[w * kRadixDigits + d] + (rd[j] >> 16);
+        hs->stage_k[pos] = key[j];
+        if constexpr (PAY) hs->stage_v[pos] = __ldcg(in_v + wbase + j * 32);
       }
     }
-    __syncthreads();
-    const unsigned cnt = (unsigned)((n - base) < (unsigned long long)kRadixTile ? (n - base) : kRadixTile);
-    for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const K k = stage_k[i];
+    half_sync(h);
+    for (unsigned i = t; i < cnt; i += kHalfThreads) {
+      const K k = hs->stage_k[i];
       const unsigned d = radix_digit(k, shift);
-      const unsigned long long dst = (unsigned long long)(unsigned)(running[d] + (i - tile_start[d]));
+      const unsigned long long dst = (unsigned long long)(unsigned)(hs->base[d] + (i - hs->tile_start[d]));
       __stcg(out_k + dst, k);
-      if constexpr (PAY) __stcg(out_v + dst, stage_v[i]);
+      if constexpr (PAY) __stcg(out_v + dst, hs->stage_v[i]);
     }
-    __syncthreads();
-    if (threadIdx.x < kRadixDigits) running[threadIdx.x] += tile_cnt[threadIdx.x];
   }
   __syncthreads();
-  return true;
+  return !ps->failed && !device_failed(c);
 }
 
 // Full LSD radix sort src -> dst (tmp as ping-pong), all CTAs.  Returns false
