@@ -157,7 +157,8 @@ cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype dtype, void
                               void* stream);
 
 /* ---- Batched form (no counterpart in the paper) -----------------------------
- * Many columns sorted by one persistent cooperative launch, one CTA per SM.
+ * Many columns sorted by one persistent cooperative launch per key type
+ * present (int32 columns, then int64 columns), one CTA per SM.
  * Each column gets exactly the result, path and report that cafs_sort_ex
  * gives it alone.  Columns with n >= grid_min_n are sorted one after another
  * by all CTAs together; the others form a work queue, longest first, from

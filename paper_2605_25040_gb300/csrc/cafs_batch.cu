@@ -1,8 +1,9 @@
 // Batched form of the CAFS sort: many columns in one persistent cooperative
-// launch (the paper sorts one array per call; batching is this library's
-// addition and leaves every column's integer result and path unchanged).
+// launch per key type (the paper sorts one array per call; batching is this
+// library's addition and leaves every column's integer result and path
+// unchanged).
 //
-// One CTA per SM.  The launch works in three stages:
+// One CTA per SM.  A launch works in three stages:
 //   1  columns with n >= grid_min_n: all CTAs sort them together, one after
 //      another, exactly like the single-column pipeline (grid barrier);
 //   2  the other columns form a work queue, longest first; each CTA takes
@@ -11,7 +12,8 @@
 //      in the radix fallback with n >= defer_min_n is put aside;
 //   3  the set-aside columns are radix-sorted by all CTAs together.
 // Every wait is bounded, as in the single-column kernels.  A plan records
-// the launch (and its zeroing memsets) once in a CUDA graph and replays it.
+// the launches (and their zeroing memsets) once in a CUDA graph and replays
+// them.
 
 #include <algorithm>
 #include <cstring>
@@ -93,33 +95,21 @@ __device__ __forceinline__ void note_failure(const BatchParams& bp, const Ctrl* 
   }
 }
 
-// The per-dtype bodies are separate calls, so that each gets a register
-// allocation of its own.
 template <typename K, class S>
-__device__ __noinline__ int body_call(const Params& p, unsigned char* smem, unsigned& epoch) {
+__device__ __forceinline__ int run_body(const Params& p, unsigned char* smem, unsigned& epoch) {
   return column_body<K>(p, smem, S(), epoch);
 }
 template <typename K, class S>
-__device__ __noinline__ bool radix_call(const Params& p, unsigned char* smem, unsigned& epoch) {
+__device__ __forceinline__ bool run_radix(const Params& p, unsigned char* smem, unsigned& epoch) {
   return column_radix<K>(p, smem, S(), epoch);
-}
-template <typename K>
-__device__ __noinline__ void small_call(const Params& p, unsigned char* smem) {
-  small_body<K>(p, smem);
-}
-
-template <class S>
-__device__ __forceinline__ int run_body(const Params& p, int dtype, unsigned char* smem, unsigned& epoch) {
-  return dtype == 1 ? body_call<long long, S>(p, smem, epoch) : body_call<int, S>(p, smem, epoch);
-}
-template <class S>
-__device__ __forceinline__ bool run_radix(const Params& p, int dtype, unsigned char* smem, unsigned& epoch) {
-  return dtype == 1 ? radix_call<long long, S>(p, smem, epoch) : radix_call<int, S>(p, smem, epoch);
 }
 
 // Set-aside list entries: a column index, with this bit for a whole column.
 constexpr unsigned kDeferWhole = 0x80000000u;
 
+// One launch per key type present in the batch (the bodies of both types in
+// one kernel would not fit the 64 registers a 1024-thread CTA can have).
+template <typename K>
 __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ Params s_p;
@@ -133,8 +123,8 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
     const BatchColumn cd = bp.cols[col];
     if (threadIdx.x == 0) s_p = column_params(cd, bp.grid_slot, bp.grid_layout, bp);
     __syncthreads();
-    int end = run_body<GridScope>(s_p, cd.dtype, smem, epoch);
-    if (end == kColumnRadix) end = run_radix<GridScope>(s_p, cd.dtype, smem, epoch) ? kColumnDone : kColumnFailed;
+    int end = run_body<K, GridScope>(s_p, smem, epoch);
+    if (end == kColumnRadix) end = run_radix<K, GridScope>(s_p, smem, epoch) ? kColumnDone : kColumnFailed;
     const bool ok = end == kColumnDone && grid_sync(gc, epoch, bp.timeout_ns);
     if (blockIdx.x == 0) {
       copy_record(bp.records + col, &gc->rec);
@@ -162,11 +152,10 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
       __syncthreads();
       int end = kColumnDone;
       if (cd.n < kSmallN) {
-        if (cd.dtype == 1) small_call<long long>(s_p, smem);
-        else small_call<int>(s_p, smem);
+        small_body<K>(s_p, smem);
       } else {
         unsigned local_epoch = 0;
-        end = run_body<CtaScope>(s_p, cd.dtype, smem, local_epoch);
+        end = run_body<K, CtaScope>(s_p, smem, local_epoch);
         if (end == kColumnTooBig) {
           // Its Eq. 6 table exceeds this slot's: all CTAs sort it in stage 3.
           if (threadIdx.x == 0) bp.deferred[atomicAdd(&bp.state->ndeferred, 1u)] = col | kDeferWhole;
@@ -176,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
             if (threadIdx.x == 0) bp.deferred[atomicAdd(&bp.state->ndeferred, 1u)] = col;
             end = kColumnDone;
           } else {
-            end = run_radix<CtaScope>(s_p, cd.dtype, smem, local_epoch) ? kColumnDone : kColumnFailed;
+            end = run_radix<K, CtaScope>(s_p, smem, local_epoch) ? kColumnDone : kColumnFailed;
           }
         }
       }
@@ -203,12 +192,12 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchParams bp) {
     __syncthreads();
     bool ok;
     if (entry & kDeferWhole) {
-      int end = run_body<GridScope>(s_p, cd.dtype, smem, epoch);
-      if (end == kColumnRadix) end = run_radix<GridScope>(s_p, cd.dtype, smem, epoch) ? kColumnDone : kColumnFailed;
+      int end = run_body<K, GridScope>(s_p, smem, epoch);
+      if (end == kColumnRadix) end = run_radix<K, GridScope>(s_p, smem, epoch) ? kColumnDone : kColumnFailed;
       ok = (end == kColumnDone) && grid_sync(gc, epoch, bp.timeout_ns);
       if (ok && blockIdx.x == 0) copy_record(bp.records + col, &gc->rec);
     } else {
-      ok = run_radix<GridScope>(s_p, cd.dtype, smem, epoch) && grid_sync(gc, epoch, bp.timeout_ns);
+      ok = run_radix<K, GridScope>(s_p, smem, epoch) && grid_sync(gc, epoch, bp.timeout_ns);
     }
     if (!ok) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -238,14 +227,21 @@ __global__ void init_slots_kernel(unsigned char* base, unsigned nslots, SlotLayo
 }
 
 cudaError_t prepare_batch_kernel() {
-  return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipelineSmem);
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipelineSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(batch_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipelineSmem);
 }
 
 cudaError_t batch_occupancy(int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, kThreads, kPipelineSmem);
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<int>, kThreads, kPipelineSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel<long long>, kThreads, kPipelineSmem);
+  *blocks_per_sm = a < b ? a : b;
+  return e;
 }
 
-cudaError_t launch_batch(const BatchParams& bp, int grid, cudaStream_t s) {
+cudaError_t launch_batch(const BatchParams& bp, int dtype, int grid, cudaStream_t s) {
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(grid);
@@ -257,7 +253,8 @@ cudaError_t launch_batch(const BatchParams& bp, int grid, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, batch_kernel, bp);
+  return dtype == 1 ? cudaLaunchKernelEx(&cfg, batch_kernel<long long>, bp)
+                    : cudaLaunchKernelEx(&cfg, batch_kernel<int>, bp);
 }
 
 // ---------------------------------------------------------------------------
@@ -397,6 +394,7 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
   s->grid_items.clear();
   s->cta_items.clear();
   s->n_max_grid = s->n_max_cta = s->sum_cta = 0;
+  s->n_grid32 = s->n_cta32 = 0;
   if (ncols && !cols) return CAFS_ERR_INVALID_ARGUMENT;
   if (ncols > 0xFFFFFFF0ull) return CAFS_ERR_TOO_LARGE;
   s->cols.resize(ncols);
@@ -427,9 +425,19 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
       s->sum_cta += c.n;
     }
   }
-  // Longest first: the queue's tail ends with the shortest columns.
-  std::stable_sort(s->cta_items.begin(), s->cta_items.end(),
-                   [&](unsigned a, unsigned b) { return s->cols[a].n > s->cols[b].n; });
+  // int32 columns first (one launch per key type), then longest first
+  // within each type: the queue's tail ends with the shortest columns.
+  auto order = [&](unsigned a, unsigned b) {
+    if (s->cols[a].dtype != s->cols[b].dtype) return s->cols[a].dtype < s->cols[b].dtype;
+    return s->cols[a].n > s->cols[b].n;
+  };
+  std::stable_sort(s->cta_items.begin(), s->cta_items.end(), order);
+  std::stable_partition(s->grid_items.begin(), s->grid_items.end(),
+                        [&](unsigned a) { return s->cols[a].dtype == 0; });
+  s->n_grid32 = (unsigned)std::count_if(s->grid_items.begin(), s->grid_items.end(),
+                                        [&](unsigned a) { return s->cols[a].dtype == 0; });
+  s->n_cta32 = (unsigned)std::count_if(s->cta_items.begin(), s->cta_items.end(),
+                                       [&](unsigned a) { return s->cols[a].dtype == 0; });
   return CAFS_OK;
 }
 
@@ -502,11 +510,11 @@ cafs_status ensure_batch(BatchBuffers* b, int grid, const Schedule& sc, const Tu
                     cudaMalloc((void**)&b->d_items, cap * sizeof(unsigned)) == cudaSuccess &&
                     cudaMalloc((void**)&b->d_deferred, cap * sizeof(unsigned)) == cudaSuccess &&
                     cudaMalloc((void**)&b->d_records, cap * sizeof(Record)) == cudaSuccess &&
-                    cudaMalloc((void**)&b->d_state, sizeof(BatchState)) == cudaSuccess &&
+                    cudaMalloc((void**)&b->d_state, 2 * sizeof(BatchState)) == cudaSuccess &&
                     cudaMallocHost((void**)&b->h_cols, cap * sizeof(BatchColumn)) == cudaSuccess &&
                     cudaMallocHost((void**)&b->h_items, cap * sizeof(unsigned)) == cudaSuccess &&
                     cudaMallocHost((void**)&b->h_records, cap * sizeof(Record)) == cudaSuccess &&
-                    (b->h_state || cudaMallocHost((void**)&b->h_state, sizeof(BatchState)) == cudaSuccess);
+                    (b->h_state || cudaMallocHost((void**)&b->h_state, 2 * sizeof(BatchState)) == cudaSuccess);
     if (!ok) {
       cudaGetLastError();
       return CAFS_ERR_OUT_OF_MEMORY;
@@ -537,21 +545,22 @@ cafs_status upload(BatchBuffers* b, const Schedule& sc, cudaStream_t s) {
   return CAFS_OK;
 }
 
-BatchParams make_params(const BatchBuffers* b, const Schedule& sc, const Tuning& t) {
+BatchParams make_params(const BatchBuffers* b, const Schedule& sc, const Tuning& t, int dtype) {
   BatchParams bp;
   std::memset(&bp, 0, sizeof(bp));
+  const size_t ng = sc.grid_items.size(), nq = sc.cta_items.size();
   bp.cols = b->d_cols;
-  bp.grid_items = b->d_items;
-  bp.cta_items = b->d_items + sc.grid_items.size();
+  bp.grid_items = b->d_items + (dtype == 1 ? sc.n_grid32 : 0u);
+  bp.cta_items = b->d_items + ng + (dtype == 1 ? sc.n_cta32 : 0u);
   bp.deferred = b->d_deferred;
   bp.records = b->d_records;
-  bp.state = b->d_state;
+  bp.state = b->d_state + dtype;
   bp.grid_slot = b->grid_slot;
   bp.cta_slots = b->cta_slots;
   bp.grid_layout = b->gl;
   bp.cta_layout = b->cl;
-  bp.n_grid = (unsigned)sc.grid_items.size();
-  bp.n_cta = (unsigned)sc.cta_items.size();
+  bp.n_grid = dtype == 1 ? (unsigned)ng - sc.n_grid32 : sc.n_grid32;
+  bp.n_cta = dtype == 1 ? (unsigned)nq - sc.n_cta32 : sc.n_cta32;
   // A queue column sorted by its own CTA's radix must fit the slot's buffer.
   bp.defer_min_n = std::min(resolve_defer(t, sc, b->grid), b->cl.n_cap + 1);
   bp.local_slots_max = t.local_slots_max;
@@ -562,14 +571,22 @@ BatchParams make_params(const BatchBuffers* b, const Schedule& sc, const Tuning&
 }
 
 // The zeroing memsets and the launch (what a plan's graph records).
-cafs_status enqueue_batch(const BatchBuffers* b, const BatchParams& bp, size_t ncols, int grid,
-                          cudaStream_t s, bool count) {
-  if (cudaMemsetAsync(b->d_state, 0, sizeof(BatchState), s) != cudaSuccess) return CAFS_ERR_CUDA;
-  if (cudaMemsetAsync(b->grid_slot + b->gl.ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+cafs_status enqueue_batch(const BatchBuffers* b, const Schedule& sc, const Tuning& t, int grid,
+                          cudaStream_t s, bool count, unsigned* launched) {
+  const size_t ncols = sc.cols.size();
+  unsigned nl = 0;
+  if (cudaMemsetAsync(b->d_state, 0, 2 * sizeof(BatchState), s) != cudaSuccess) return CAFS_ERR_CUDA;
   if (ncols && cudaMemsetAsync(b->d_records, 0, ncols * sizeof(Record), s) != cudaSuccess) return CAFS_ERR_CUDA;
-  if (bp.n_grid == 0 && bp.n_cta == 0) return CAFS_OK;
-  if (launch_batch(bp, grid, s) != cudaSuccess) return CAFS_ERR_CUDA;
-  if (count) count_launches(1);
+  for (int dtype = 0; dtype < 2; ++dtype) {
+    const BatchParams bp = make_params(b, sc, t, dtype);
+    if (bp.n_grid == 0 && bp.n_cta == 0) continue;
+    // the grid barrier's words start from zero in every launch
+    if (cudaMemsetAsync(b->grid_slot + b->gl.ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+    if (launch_batch(bp, dtype, grid, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    ++nl;
+  }
+  if (count) count_launches(nl);
+  if (launched) *launched = nl;
   return CAFS_OK;
 }
 
@@ -578,10 +595,11 @@ cafs_status read_reports(BatchBuffers* b, const Schedule& sc, cafs_report* repor
   const size_t ncols = sc.cols.size();
   if (ncols && cudaMemcpyAsync(b->h_records, b->d_records, ncols * sizeof(Record), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return CAFS_ERR_CUDA;
-  if (cudaMemcpyAsync(b->h_state, b->d_state, sizeof(BatchState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (cudaMemcpyAsync(b->h_state, b->d_state, 2 * sizeof(BatchState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return CAFS_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CAFS_ERR_CUDA;
-  const BatchState st = *b->h_state;
+  BatchState st = b->h_state[0];
+  if (st.status == kDevOk) st.status = b->h_state[1].status;
   for (size_t i = 0; i < ncols; ++i) {
     if (sc.cols[i].n == 0) {
       std::memset(&reports[i], 0, sizeof(cafs_report));
@@ -605,7 +623,7 @@ struct cafs_batch_plan {
   Tuning tuning;
   Schedule sched;
   BatchBuffers buf;
-  BatchParams bp;
+  unsigned launches = 0;   // kernels one replay launches
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::mutex mu;
@@ -644,8 +662,7 @@ cafs_status cafs_sort_batch_tuned(const cafs_column* cols, size_t ncols, const c
   }
   if ((st = ensure_batch(b, grid, sc, t, s)) != CAFS_OK) return st;
   if ((st = upload(b, sc, s)) != CAFS_OK) return st;
-  const BatchParams bp = make_params(b, sc, t);
-  if ((st = enqueue_batch(b, bp, sc.cols.size(), grid, s, true)) != CAFS_OK) return st;
+  if ((st = enqueue_batch(b, sc, t, grid, s, true, nullptr)) != CAFS_OK) return st;
   if (reports) return read_reports(b, sc, reports, s);
   return CAFS_OK;
 }
@@ -685,11 +702,11 @@ cafs_status cafs_batch_plan_create(const cafs_column* cols, size_t ncols, const 
   if ((st = ensure_batch(&pl->buf, grid, pl->sched, pl->tuning, s)) != CAFS_OK) return fail(st);
   if ((st = upload(&pl->buf, pl->sched, s)) != CAFS_OK) return fail(st);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(CAFS_ERR_CUDA);
-  pl->bp = make_params(&pl->buf, pl->sched, pl->tuning);
+
   // Record the memsets and the cooperative launch once.
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(CAFS_ERR_CUDA);
   // (Capturing launches nothing; the launch counter counts the replays.)
-  st = enqueue_batch(&pl->buf, pl->bp, pl->sched.cols.size(), grid, s, false);
+  st = enqueue_batch(&pl->buf, pl->sched, pl->tuning, grid, s, false, &pl->launches);
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(s, &g);
   pl->graph = g;
@@ -714,7 +731,7 @@ cafs_status cafs_batch_plan_launch(cafs_batch_plan* pl, void* stream) {
   if (cudaGetDevice(&dev) != cudaSuccess) return CAFS_ERR_CUDA;
   if (dev != pl->device) return CAFS_ERR_INVALID_ARGUMENT;
   if (cudaGraphLaunch(pl->exec, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return CAFS_ERR_CUDA;
-  if (pl->bp.n_grid || pl->bp.n_cta) count_launches(1);
+  count_launches(pl->launches);
   return CAFS_OK;
 }
 

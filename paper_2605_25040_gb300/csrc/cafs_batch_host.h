@@ -34,7 +34,7 @@ struct BatchBuffers {
   unsigned* d_items = nullptr;      // grid items, then queue items
   unsigned* d_deferred = nullptr;
   Record* d_records = nullptr;
-  BatchState* d_state = nullptr;
+  BatchState* d_state = nullptr;    // one per key type
   BatchColumn* h_cols = nullptr;    // pinned staging
   unsigned* h_items = nullptr;
   Record* h_records = nullptr;
@@ -53,6 +53,7 @@ struct Schedule {
   std::vector<unsigned> grid_items, cta_items;
   unsigned long long n_max_grid = 0, n_max_cta = 0;
   unsigned long long sum_cta = 0;   // keys in the per-CTA queue
+  unsigned n_grid32 = 0, n_cta32 = 0;   // int32 items come first in each list
 };
 
 // Validates and converts the public knobs (NULL = defaults).
@@ -75,9 +76,10 @@ cafs_status ensure_batch(BatchBuffers* b, int grid, const Schedule& sc, const Tu
 void free_batch(BatchBuffers* b);
 // Copies the schedule's descriptors to the device (asynchronously on s).
 cafs_status upload(BatchBuffers* b, const Schedule& sc, cudaStream_t s);
-BatchParams make_params(const BatchBuffers* b, const Schedule& sc, const Tuning& t);
-// The zeroing memsets and the cooperative launch.
-cafs_status enqueue_batch(const BatchBuffers* b, const BatchParams& bp, size_t ncols, int grid,
-                          cudaStream_t s, bool count);
+// Launch parameters for the columns of one key type (0 int32, 1 int64).
+BatchParams make_params(const BatchBuffers* b, const Schedule& sc, const Tuning& t, int dtype);
+// The zeroing memsets and one cooperative launch per key type present.
+cafs_status enqueue_batch(const BatchBuffers* b, const Schedule& sc, const Tuning& t, int grid,
+                          cudaStream_t s, bool count, unsigned* launched);
 
 }  // namespace cafs

@@ -260,7 +260,7 @@ cudaError_t launch_fill_u64(unsigned long long* ptr, unsigned long long n, unsig
                             cudaStream_t s);
 cudaError_t prepare_batch_kernel();
 cudaError_t batch_occupancy(int* blocks_per_sm);
-cudaError_t launch_batch(const BatchParams& bp, int grid, cudaStream_t s);
+cudaError_t launch_batch(const BatchParams& bp, int dtype, int grid, cudaStream_t s);
 
 // Shared by the host entry points (defined in cafs_api.cu).
 void count_launches(unsigned k);

@@ -860,6 +860,7 @@ __device__ void phase_rank_pairs(const Params& p, unsigned occ, unsigned long lo
     const long long ki = jk[i];
     unsigned rk = 0;
     unsigned long long off = 0;
+    #pragma unroll 4
     for (unsigned j = lane; j < occ; j += 32) {
       const bool lt = jk[j] < ki;
       rk += lt ? 1u : 0u;
@@ -942,7 +943,7 @@ struct HalfSmem {
   unsigned short wcnt[kHalfWarps * kRadixDigits];
   unsigned tile_cnt[kRadixDigits];
   unsigned tile_start[kRadixDigits];
-  unsigned base[kRadixDigits];
+  unsigned base[kRadixDigits];      // digit destination minus its first stage slot
   unsigned scratch[kHalfWarps];
   unsigned scan_part[kHalfThreads];
 };
@@ -1121,7 +1122,7 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     half_sync(h);
     if (*reinterpret_cast<volatile unsigned*>(&ps->failed)) break;
     if (t < kRadixDigits) {
-      hs->base[t] = running[t];
+      hs->base[t] = running[t] - hs->tile_start[t];   // destination of stage slot i = base[d] + i
       running[t] += hs->tile_cnt[t];
     }
     half_sync(h);
@@ -1143,7 +1144,7 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     for (unsigned i = t; i < cnt; i += kHalfThreads) {
       const K k = hs->stage_k[i];
       const unsigned d = radix_digit(k, shift);
-      const unsigned long long dst = (unsigned long long)(unsigned)(hs->base[d] + (i - hs->tile_start[d]));
+      const unsigned long long dst = (unsigned long long)(unsigned)(hs->base[d] + i);
       __stcg(out_k + dst, k);
       if constexpr (PAY) __stcg(out_v + dst, hs->stage_v[i]);
     }
@@ -1489,10 +1490,21 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
   else phase_count<K, false>(p, keys, smem, ring, sc);
   if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
   mark(c, 3, sc);
-  const unsigned occ = ld_relaxed_u32(&c->occupancy);
-  const unsigned long long special = ld_relaxed_u64(&c->special);
+  // One thread per CTA reads the counters every CTA hammered with atomics;
+  // the others take them from shared memory (1024 reads of one hot L2 line
+  // per CTA cost several microseconds).
+  unsigned long long* cnt_smem = reinterpret_cast<unsigned long long*>(smem + kPipelineSmem - 64);
+  if (threadIdx.x == 0) {
+    cnt_smem[0] = ld_relaxed_u32(&c->occupancy);
+    cnt_smem[1] = ld_relaxed_u64(&c->special);
+    cnt_smem[2] = ld_relaxed_u32(&c->overflow);
+  }
+  __syncthreads();
+  const unsigned occ = (unsigned)cnt_smem[0];
+  const unsigned long long special = cnt_smem[1];
   const unsigned long long kp = (unsigned long long)occ + (special ? 1ull : 0ull);
-  const bool overflow = ld_relaxed_u32(&c->overflow) != 0u || kp > r.L;
+  const bool overflow = cnt_smem[2] != 0ull || kp > r.L;
+  __syncthreads();
   // Sec. 4.4: the tiny counters add up to N exactly when every key is one
   // of the u sampled keys, i.e. when the column has exactly u distinct keys.
   int path;

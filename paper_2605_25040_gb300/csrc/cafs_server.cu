@@ -190,14 +190,11 @@ void scheduler_loop(cafs_server* sv) {
       st = CAFS_ERR_CUDA;
     if (st == CAFS_OK) st = make_schedule(cols.data(), cols.size(), sv->tuning, sv->grid, &sc);
     if (st == CAFS_OK) st = upload(&sv->buf, sc, sv->s_run);
-    if (st == CAFS_OK) {
-      const BatchParams bp = make_params(&sv->buf, sc, sv->tuning);
-      st = enqueue_batch(&sv->buf, bp, sc.cols.size(), sv->grid, sv->s_run, true);
-    }
+    if (st == CAFS_OK) st = enqueue_batch(&sv->buf, sc, sv->tuning, sv->grid, sv->s_run, true, nullptr);
     if (st == CAFS_OK &&
         (cudaMemcpyAsync(L->h_records, sv->buf.d_records, batch.size() * sizeof(Record),
                          cudaMemcpyDeviceToHost, sv->s_run) != cudaSuccess ||
-         cudaMemcpyAsync(L->h_state, sv->buf.d_state, sizeof(BatchState), cudaMemcpyDeviceToHost,
+         cudaMemcpyAsync(L->h_state, sv->buf.d_state, 2 * sizeof(BatchState), cudaMemcpyDeviceToHost,
                          sv->s_run) != cudaSuccess ||
          cudaEventRecord(sv->ev_run, sv->s_run) != cudaSuccess ||
          cudaStreamWaitEvent(sv->s_out, sv->ev_run, 0) != cudaSuccess))
@@ -232,7 +229,8 @@ void completion_loop(cafs_server* sv) {
     const double t = now_s();
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      const BatchState st = *L->h_state;
+      BatchState st = L->h_state[0];
+      if (st.status == kDevOk) st.status = L->h_state[1].status;
       for (size_t i = 0; i < L->reqs.size(); ++i) {
         Request* r = L->reqs[i];
         fill_report(L->h_records[i], &r->report);
@@ -367,7 +365,7 @@ cafs_status cafs_server_create(size_t mem_budget_bytes, const cafs_server_config
     sv->free_launches.push_back(L);
     if (cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost((void**)&L->h_records, sv->max_batch * sizeof(Record)) != cudaSuccess ||
-        cudaMallocHost((void**)&L->h_state, sizeof(BatchState)) != cudaSuccess)
+        cudaMallocHost((void**)&L->h_state, 2 * sizeof(BatchState)) != cudaSuccess)
       return fail(CAFS_ERR_OUT_OF_MEMORY);
   }
   sv->sched = std::thread(scheduler_loop, sv);
