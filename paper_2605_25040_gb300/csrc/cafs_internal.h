@@ -43,6 +43,10 @@ constexpr int kChunkBytes = kChunkVecs * 16;
 // phase's tables below it.
 constexpr int kRingStages = 4;
 constexpr int kRingBytes = kRingStages * kChunkBytes;
+// Just below the ring: its mbarriers (full and empty per stage) and the
+// shared copy of the skip flag.
+constexpr int kRingReserve = 256;
+static_assert(2 * kRingStages * 8 + 4 <= kRingReserve, "ring barriers below the ring");
 // Shared-memory budget of the per-CTA hash table (keys + counters), of the
 // small bookkeeping area before it, and of the tiny path's table (the tiny
 // path's per-thread bucket counters follow it inside the table budget).

@@ -267,10 +267,9 @@ struct Ring {
   __device__ void start(const Params& p, const K* keys, unsigned char* smem, const S& sc) {
     const Share<K> sh(keys, p.n, sc);
     buf = smem + (kPipelineSmem - kRingBytes);
-    full = reinterpret_cast<unsigned long long*>(buf - 128);
+    full = reinterpret_cast<unsigned long long*>(buf - kRingReserve);
     empty = full + kRingStages;
     skip_flag = reinterpret_cast<unsigned*>(empty + kRingStages);
-    static_assert(2 * kRingStages * 8 + 4 <= 128, "ring barriers and flag below the ring");
     src = reinterpret_cast<const unsigned char*>(keys + sh.head) + sh.v0 * 16ull;
     total = (sh.v1 - sh.v0) * 16ull;
     nchunks = (total + kChunkBytes - 1) / kChunkBytes;
@@ -699,8 +698,8 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
   unsigned* local_occ = reinterpret_cast<unsigned*>(mbase);                       // 1
   unsigned long long* red = reinterpret_cast<unsigned long long*>(mbase + 8);     // kWarps
   K* tkey = reinterpret_cast<K*>(mbase + 8 + 8 * kWarps);                          // kTinyBuckets
-  static_assert(kLocalTableBytes + kMiscBytes + 128 <= kPipelineSmem - kRingBytes, "table under ring");
-  static_assert(kTinyTableBytes + kTinyBuckets * kConsumerWarps * 32 * 4 + kMiscBytes + 128 <=
+  static_assert(kLocalTableBytes + kMiscBytes + kRingReserve <= kPipelineSmem - kRingBytes, "table under ring");
+  static_assert(kTinyTableBytes + kTinyBuckets * kConsumerWarps * 32 * 4 + kMiscBytes + kRingReserve <=
                     kPipelineSmem - kRingBytes, "tiny table under ring");
 
   const int nt = r.n_tiny;
