@@ -139,7 +139,7 @@ struct Params {
   void* tmp;
   unsigned long long* lookback;       // radix scratch: per-CTA digit counts and bases
   unsigned long long lookback_cap;   // words
-  long long* sample_keys;            // kSamples: distinct sampled keys, ascending
+  long long* sample_keys;            // kSamples: distinct sampled keys (FreqSet slot order)
   unsigned gen;          // call counter (diagnostic)
   int mode;
   unsigned test_flags;

@@ -47,8 +47,28 @@ namespace cafs {
 // ---------------------------------------------------------------------------
 // Phase 0: sampler, spectrum, Chao1, Eq. 6, provisional dispatch (one CTA).
 // ---------------------------------------------------------------------------
+// The strided samples of Alg. 2 that fall in part `part` of `nparts`: part b
+// loads samples [1024 b / nparts, 1024 (b + 1) / nparts), which lie in its own
+// share of the column, into `buf` (global).
 template <typename K>
-__device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem) {
+__device__ __forceinline__ void gather_samples(const Params& p, const K* keys, long long* buf,
+                                               unsigned part, unsigned nparts) {
+  const unsigned long long n = p.n;
+  const unsigned long long stride = n / kSamples > 0 ? n / kSamples : 1ull;
+  const int ns = n < (unsigned long long)kSamples ? (int)n : kSamples;
+  const int i0 = (int)((unsigned long long)ns * part / nparts);
+  const int i1 = (int)((unsigned long long)ns * (part + 1) / nparts);
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += kThreads)
+    buf[i] = (long long)keys[(unsigned long long)i * stride];
+}
+
+// Every CTA that calls this computes the same record, sample-key list and
+// tiny-path multiplier from the same samples (all orders are deterministic),
+// so the grid needs no barrier after it.  `gathered` (global, may be null)
+// holds the samples already; otherwise they are read from the column.
+template <typename K>
+__device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem,
+                             const long long* gathered = nullptr) {
   using T = KeyTraits<K>;
   // Algorithm 2's FreqSet: a 4096-slot open-addressing table in shared
   // memory, filled with the 1024 strided samples in parallel.  The empty
@@ -69,9 +89,9 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
     fcnt[i] = 0u;
   }
   if (t == 0) scratch[kWarps] = 0;        // samples equal to the type minimum
-  if (t == 0) scratch[kWarps + 1] = 0;    // next free index in the distinct list
   for (int i = t; i < kSamples; i += kThreads)
-    s[i] = i < ns ? (long long)keys[(unsigned long long)i * stride] : LLONG_MAX;
+    s[i] = i < ns ? (gathered ? __ldcg(gathered + i) : (long long)keys[(unsigned long long)i * stride])
+                  : LLONG_MAX;
   __syncthreads();
   int asc = 1;
   for (int i = t; i + 1 < ns; i += kThreads) asc &= (s[i] <= s[i + 1]);
@@ -114,13 +134,29 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
   // (they seed the count tables), and when u <= 8 also to the record (tiny
   // path).
   Record& r = p.ctrl->rec;
-  for (int i = t; i < kFreqSlots + 1; i += kThreads) {
-    const bool occupied = i < kFreqSlots ? fcnt[i] > 0u : nmin > 0;
-    if (occupied) {
-      const long long v = i < kFreqSlots ? fkey[i] : kmin;
-      const int idx = atomicAdd(scratch + kWarps + 1, 1);
-      if (p.sample_keys) p.sample_keys[idx] = v;
-      if (u <= kTinyMax) r.tiny_keys[idx] = v;
+  {
+    // Slot order (a block scan over the occupancy of each thread's slots),
+    // so that every CTA computing this writes the same list.
+    constexpr int kPer = (kFreqSlots + kThreads - 1) / kThreads + 1;
+    int occ_mine = 0;
+    #pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = t * kPer + q;
+      if (i < kFreqSlots) occ_mine += fcnt[i] > 0u;
+      else if (i == kFreqSlots) occ_mine += nmin > 0;
+    }
+    int tot_unused;
+    int idx = block_exclusive_scan(occ_mine, scratch, &tot_unused);
+    #pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = t * kPer + q;
+      const bool occupied = i < kFreqSlots ? fcnt[i] > 0u : (i == kFreqSlots && nmin > 0);
+      if (occupied) {
+        const long long v = i < kFreqSlots ? fkey[i] : kmin;
+        if (p.sample_keys) p.sample_keys[idx] = v;
+        if (u <= kTinyMax) r.tiny_keys[idx] = v;
+        ++idx;
+      }
     }
   }
   // Tiny path: find an odd multiplier that sends the u <= 8 sampled keys to
@@ -1404,15 +1440,6 @@ __device__ __forceinline__ void mark(Ctrl* c, int i, const S& sc) {
   if (sc.lead()) c->rec.timeline[i] = global_timer_ns();
 }
 
-// Head start of the sampling CTA's loads over the other CTAs' ring (ns).
-constexpr unsigned long long kSampleHeadStartNs = 2500;
-
-// Waits about `ns` nanoseconds (global timer).
-__device__ __forceinline__ void spin_ns(unsigned long long ns) {
-  const unsigned long long t0 = global_timer_ns();
-  while (global_timer_ns() - t0 < ns) __nanosleep(200);
-}
-
 // How a column's pass through column_body() ended.
 enum ColumnEnd : int {
   kColumnDone = 0,     // output written
@@ -1435,23 +1462,24 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
   const K* keys = reinterpret_cast<const K*>(p.keys);
   K* out = reinterpret_cast<K*>(p.out);
 
-  // The count phase's first chunks are on their way while part 0 samples.
-  // With the whole grid on one column, the sampling CTA's 1024 strided
-  // loads go first: it starts its own ring after sampling, and the other
-  // CTAs start theirs after a short head start (their first chunks still
-  // land long before counting begins; queued behind them, the samples took
-  // about 8 us instead of 2).
+  // The count phase's first chunks are on their way while the samples are
+  // taken.  With the whole grid on one column, every CTA fetches the samples
+  // that lie in its own share (one CTA reading all 1024 strided positions,
+  // spread over the whole column, spent about 8 us in address-translation
+  // misses), then every CTA computes the estimate itself: one barrier, and
+  // counting starts right after it.
   constexpr bool kGrid = std::is_same<S, GridScope>::value;
-  const bool sampler = sc.part() == 0;
   Ring<K> ring;
   ring.live = false;
-  if (p.mode == kModeSort && !(kGrid && sampler)) {
-    if (kGrid) spin_ns(kSampleHeadStartNs);
-    ring.start(p, keys, smem, sc);
+  if (p.mode == kModeSort) ring.start(p, keys, smem, sc);
+  if constexpr (kGrid) {
+    long long* gathered = reinterpret_cast<long long*>(p.lookback);
+    gather_samples<K>(p, keys, gathered, sc.part(), sc.nparts());
+    if (!sc.sync(c, epoch, p.timeout_ns)) { ring.drain(p); return kColumnFailed; }
+    phase_sample<K>(p, keys, smem, gathered);
+  } else {
+    phase_sample<K>(p, keys, smem);
   }
-  if (sampler) phase_sample<K>(p, keys, smem);
-  if (kGrid && sampler && p.mode == kModeSort) ring.start(p, keys, smem, sc);
-  if (!sc.sync(c, epoch, p.timeout_ns)) { ring.drain(p); return kColumnFailed; }
   mark(c, 1, sc);
 
   Record& r = c->rec;
