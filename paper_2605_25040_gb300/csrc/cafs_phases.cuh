@@ -63,9 +63,19 @@ __device__ __forceinline__ void gather_samples(const Params& p, const K* keys, l
 }
 
 // Every CTA that calls this computes the same record, sample-key list and
-// tiny-path multiplier from the same samples (all orders are deterministic),
-// so the grid needs no barrier after it.  `gathered` (global, may be null)
+// tiny-path multiplier from the same samples, so the grid needs no barrier
+// after it: the spectrum does not depend on where the parallel inserts put
+// the keys, and the distinct keys are listed in the order of their first
+// sample position (the FreqSet's slot order would depend on which of two
+// colliding keys was inserted first).  `gathered` (global, may be null)
 // holds the samples already; otherwise they are read from the column.
+constexpr int kFreqSlots = 4096;
+// FreqSet keys, counts and first positions, the samples, each sample's slot,
+// the scratch words.
+constexpr int kSampleSmem = kFreqSlots * (8 + 4 + 4) + kSamples * (8 + 4) + 256;
+static_assert(kSamples == kThreads, "one sample position per thread in the listing scan");
+static_assert(kSampleSmem + kRingReserve <= kPipelineSmem - kRingBytes, "sampler below the ring");
+
 template <typename K>
 __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem,
                              const long long* gathered = nullptr) {
@@ -73,11 +83,12 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
   // Algorithm 2's FreqSet: a 4096-slot open-addressing table in shared
   // memory, filled with the 1024 strided samples in parallel.  The empty
   // marker is the type minimum; samples equal to it are counted on the side.
-  constexpr int kFreqSlots = 4096;
   long long* fkey = reinterpret_cast<long long*>(smem);                 // kFreqSlots
   unsigned* fcnt = reinterpret_cast<unsigned*>(fkey + kFreqSlots);      // kFreqSlots
-  long long* s = reinterpret_cast<long long*>(fcnt + kFreqSlots);       // kSamples, position order
-  int* scratch = reinterpret_cast<int*>(s + kSamples);                  // kWarps + 2
+  int* ffirst = reinterpret_cast<int*>(fcnt + kFreqSlots);              // kFreqSlots: first position
+  long long* s = reinterpret_cast<long long*>(ffirst + kFreqSlots);     // kSamples, position order
+  int* sslot = reinterpret_cast<int*>(s + kSamples);                    // kSamples: slot of each sample
+  int* scratch = sslot + kSamples;                                      // kWarps + 2
   const int t = threadIdx.x;
   const unsigned long long n = p.n;
   const unsigned long long stride = n / kSamples > 0 ? n / kSamples : 1ull;
@@ -87,8 +98,12 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
   for (int i = t; i < kFreqSlots; i += kThreads) {
     fkey[i] = kmin;
     fcnt[i] = 0u;
+    ffirst[i] = INT_MAX;
   }
-  if (t == 0) scratch[kWarps] = 0;        // samples equal to the type minimum
+  if (t == 0) {
+    scratch[kWarps] = 0;              // samples equal to the type minimum
+    scratch[kWarps + 1] = INT_MAX;    // first position of such a sample
+  }
   for (int i = t; i < kSamples; i += kThreads)
     s[i] = i < ns ? (gathered ? __ldcg(gathered + i) : (long long)keys[(unsigned long long)i * stride])
                   : LLONG_MAX;
@@ -102,6 +117,8 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
     const long long x = s[i];
     if (x == kmin) {
       atomicAdd(scratch + kWarps, 1);
+      atomicMin(scratch + kWarps + 1, i);
+      sslot[i] = -1;
       continue;
     }
     unsigned slot = (unsigned)hash_slot((unsigned long long)x, 12);
@@ -115,6 +132,8 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
       }
     }
     atomicAdd(fcnt + slot, 1u);
+    atomicMin(ffirst + slot, i);
+    sslot[i] = (int)slot;
   }
   __syncthreads();
   // Spectrum: occupied slots (u), slots seen once (f1) and twice (f2).
@@ -130,32 +149,24 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
   const int f1 = block_sum(c1, scratch) + (nmin == 1);
   const int f2 = block_sum(c2, scratch) + (nmin == 2);
 
-  // The distinct sample values (unordered): all of them go to the workspace
-  // (they seed the count tables), and when u <= 8 also to the record (tiny
-  // path).
+  // The distinct sample values in the order of their first sample position
+  // (a block scan over the positions, one per thread): all of them go to
+  // the workspace (they seed the count tables), and when u <= 8 also to the
+  // record (tiny path).
   Record& r = p.ctrl->rec;
+  long long* tiny_list = reinterpret_cast<long long*>(fkey);   // reuses the FreqSet keys
   {
-    // Slot order (a block scan over the occupancy of each thread's slots),
-    // so that every CTA computing this writes the same list.
-    constexpr int kPer = (kFreqSlots + kThreads - 1) / kThreads + 1;
-    int occ_mine = 0;
-    #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = t * kPer + q;
-      if (i < kFreqSlots) occ_mine += fcnt[i] > 0u;
-      else if (i == kFreqSlots) occ_mine += nmin > 0;
-    }
+    const int i = t;   // kSamples == kThreads
+    bool first = false;
+    if (i < ns) first = sslot[i] < 0 ? scratch[kWarps + 1] == i : ffirst[sslot[i]] == i;
     int tot_unused;
-    int idx = block_exclusive_scan(occ_mine, scratch, &tot_unused);
-    #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = t * kPer + q;
-      const bool occupied = i < kFreqSlots ? fcnt[i] > 0u : (i == kFreqSlots && nmin > 0);
-      if (occupied) {
-        const long long v = i < kFreqSlots ? fkey[i] : kmin;
-        if (p.sample_keys) p.sample_keys[idx] = v;
-        if (u <= kTinyMax) r.tiny_keys[idx] = v;
-        ++idx;
+    const int idx = block_exclusive_scan(first ? 1 : 0, scratch, &tot_unused);   // barrier first
+    if (first) {
+      const long long v = s[i];
+      if (p.sample_keys) p.sample_keys[idx] = v;
+      if (u <= kTinyMax) {
+        r.tiny_keys[idx] = v;
+        tiny_list[idx] = v;
       }
     }
   }
@@ -166,7 +177,7 @@ __device__ void phase_sample(const Params& p, const K* keys, unsigned char* smem
     unsigned long long tkv[kTinyMax];
     #pragma unroll
     for (int j = 0; j < kTinyMax; ++j)
-      tkv[j] = j < u ? (unsigned long long)(typename T::U)(K)r.tiny_keys[j] : 0ull;
+      tkv[j] = j < u ? (unsigned long long)(typename T::U)(K)tiny_list[j] : 0ull;
     bool found = false;
     for (int round = 0; round < 16 && !found; ++round) {
       const unsigned long long m = (kPhi * (2ull * (unsigned long long)(round * 32 + t) + 1ull)) | 1ull;
@@ -1615,9 +1626,9 @@ __device__ void small_body(const Params& p, unsigned char* smem) {
   __syncthreads();
 }
 
-// The N < 2048 kernel needs the sampler's FreqSet (4096 x 12 B + samples)
+// The N < 2048 kernel needs the sampler's shared memory (kSampleSmem)
 // and later the column itself (kSmallCap x 8 B).
-constexpr int kSmallSmem = 4096 * 12 + kSamples * 8 + 1024;
+constexpr int kSmallSmem = kSampleSmem + 1024;
 static_assert(kSmallSmem >= kSmallCap * 8, "small-kernel shared memory");
 
 }  // namespace cafs

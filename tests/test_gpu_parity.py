@@ -211,3 +211,59 @@ def test_emit_tiles_with_a_few_short_runs(dtype, offset):
                  [16_381, 3, 16_000, 5, 7, 30_000]):
         x = np.repeat(np.arange(len(lens), dtype=dtype) * 7 - 3, lens)
         check_sort(G.shuffle(x, sum(lens)), offset=offset)
+
+
+def eq4_slots(x: np.ndarray, log2size: int) -> np.ndarray:
+    """Eq. 4 for the test data: ((x * 2^64/phi) mod 2^64) >> (64 - log2 M),
+    x taken as its 64-bit two's-complement pattern (int32 sign-extended)."""
+    u = x.astype(np.int64).view(np.uint64)
+    with np.errstate(over="ignore"):
+        return (u * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(64 - log2size)
+
+
+def colliding_values(groups: int, per_group: int, dtype, seed: int) -> np.ndarray:
+    """groups x per_group distinct values; the values of a group share one
+    slot of a 4096-slot Eq. 4 table (Alg. 2's FreqSet), so where each lands
+    depends on which is inserted first."""
+    rng = np.random.default_rng(seed)
+    info = np.iinfo(dtype)
+    cand = np.unique(rng.integers(info.min + 1, info.max, size=400_000, dtype=dtype))
+    slots = eq4_slots(cand, 12)
+    order = np.argsort(slots, kind="stable")
+    s_sorted = slots[order]
+    starts = np.flatnonzero(np.r_[True, s_sorted[1:] != s_sorted[:-1]])
+    ends = np.r_[starts[1:], s_sorted.size]
+    full = [(a, b) for a, b in zip(starts, ends) if b - a >= per_group][:groups]
+    assert len(full) == groups
+    return np.concatenate([cand[order[a:a + per_group]] for a, _ in full])
+
+
+def place_samples_by_warp(x: np.ndarray, vals: np.ndarray) -> np.ndarray:
+    """Alg. 2's strided sample positions i * stride (i < 1024) get vals[i //
+    (1024 / len(vals))]: each value's samples are contiguous, so different
+    warps of the sampler insert different values of a colliding group."""
+    x = x.copy()
+    stride = max(1, x.size // 1024)
+    i = np.arange(1024)
+    x[i * stride] = vals[i * len(vals) // 1024]
+    return x
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_sampled_keys_colliding_in_the_sampler_table(dtype):
+    # Every CTA of the grid computes the estimate and the list of sampled keys
+    # itself; the list (and the tiny path's keys) must not depend on the
+    # order in which colliding keys entered the FreqSet.  Repeated calls.
+    vals8 = colliding_values(1, 8, dtype, seed=11)
+    rng = np.random.default_rng(13)
+    x = place_samples_by_warp(vals8[rng.integers(0, 8, size=300_000)], vals8)
+    vals = colliding_values(32, 8, dtype, seed=12)
+    y = place_samples_by_warp(vals[rng.integers(0, vals.size, size=300_000)], vals)
+    for _ in range(8):
+        assert check_sort(x)["path"] == O.TINY
+        assert check_sort(y)["path"] == O.MAIN
+    outs, reps = cafs.sort_batch([torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()] * 4,
+                                 reports=True, tuning={"grid_min_n": 2048})
+    for o, r, z in zip(outs, reps, [x, y] * 4):
+        assert np.array_equal(o.cpu().numpy(), O.frequency_sort(z))
+        assert r["path"] == O.final_path(z)
