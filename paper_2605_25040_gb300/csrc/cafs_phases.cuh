@@ -957,6 +957,50 @@ __device__ __forceinline__ void half_sync(int h) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(kHalfThreads) : "memory");
 }
 
+// Lanes of the warp whose digit equals this lane's (digits < 2^9: the
+// radix digit, or 256 for no item), from one ballot per digit bit.  A
+// warp-wide match costs more the more distinct values the warp holds; the
+// ballots cost the same for any mix, which wins on the well-mixed digits of
+// high-entropy passes.  `all_valid`: every lane holds an item (digit < 256).
+__device__ __forceinline__ unsigned digit_peers_ballot(unsigned d, bool all_valid) {
+  unsigned peers = 0xffffffffu;
+  #pragma unroll
+  for (int bit = 0; bit < kRadixBits; ++bit) {
+    const unsigned on = (d >> bit) & 1u;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    peers &= on ? b : ~b;
+  }
+  if (!all_valid) {
+    const unsigned on = (d >> kRadixBits) & 1u;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    peers &= on ? b : ~b;
+  }
+  return peers;
+}
+
+// Stable rank of a warp's items within the warp (item-major, then lane):
+// rd[j] holds the digit on entry and gets (rank << 16) | digit.  `row` is
+// the warp's digit-counter row (zero on entry, the warp's digit counts on
+// exit).
+template <bool kMatch>
+__device__ __forceinline__ void rank_warp_items(unsigned (&rd)[kRadixItems], unsigned short* row,
+                                                int lane, bool all_valid) {
+  #pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    const unsigned d = rd[j];
+    const unsigned peers = kMatch ? __match_any_sync(0xffffffffu, d) : digit_peers_ballot(d, all_valid);
+    const int leader = __ffs(peers) - 1;
+    unsigned old = 0;
+    if (lane == leader && d < (unsigned)kRadixDigits) {
+      old = row[d];
+      row[d] = (unsigned short)(old + __popc(peers));
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    __syncwarp();
+    rd[j] = d | ((old + __popc(peers & lanemask_lt())) << 16);
+  }
+}
+
 // Exclusive scan of one value per thread of a half (all its threads call it).
 __device__ __forceinline__ unsigned half_exclusive_scan(unsigned v, unsigned* scratch, int h) {
   const int t = threadIdx.x - h * kHalfThreads, w = t >> 5, l = t & 31;
@@ -1101,20 +1145,15 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
       key[j] = valid ? __ldcg(in_k + idx) : (K)0;
       rd[j] = valid ? radix_digit(key[j], shift) : (unsigned)kRadixDigits;
     }
-    #pragma unroll
-    for (int j = 0; j < kRadixItems; ++j) {
-      const unsigned d = rd[j];
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const int leader = __ffs(peers) - 1;
-      unsigned old = 0;
-      if (lane == leader && d < (unsigned)kRadixDigits) {
-        old = hs->wcnt[w * kRadixDigits + d];
-        hs->wcnt[w * kRadixDigits + d] = (unsigned short)(old + __popc(peers));
-      }
-      old = __shfl_sync(0xffffffffu, old, leader);
-      __syncwarp();
-      rd[j] = d | ((old + __popc(peers & lanemask_lt())) << 16);
-    }
+    // Runs of equal keys (a later pass over repeated keys) leave few
+    // distinct digits per warp, where the match instruction is cheaper than
+    // the ballots: the warp picks one by how many lanes share the digit of
+    // the next lane (item 0).
+    const bool full_tile = cnt == (unsigned)kHalfTile;
+    const unsigned next_d = __shfl_down_sync(0xffffffffu, rd[0], 1);
+    const bool runs = __popc(__ballot_sync(0xffffffffu, lane == 31 || next_d == rd[0])) >= 16;
+    if (runs) rank_warp_items<true>(rd, hs->wcnt + w * kRadixDigits, lane, full_tile);
+    else rank_warp_items<false>(rd, hs->wcnt + w * kRadixDigits, lane, full_tile);
     half_sync(h);
     // Per digit: exclusive scan over the half's warps and the half-tile total.
     {
