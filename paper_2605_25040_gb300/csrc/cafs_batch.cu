@@ -82,6 +82,8 @@ __device__ __forceinline__ void clear_column_state(Ctrl* c) {
     c->overflow = 0u;
     c->inversion = 0u;
     c->special = 0ull;
+    c->key_or = 0ull;
+    c->key_nor = 0ull;
   }
   unsigned* h = &c->hist[0][0];
   for (int i = threadIdx.x; i < 8 * kRadixDigits; i += blockDim.x) h[i] = 0u;
@@ -269,7 +271,7 @@ SlotLayout slot_layout(unsigned long long table_cap, unsigned long long tmp_keys
   std::memset(&L, 0, sizeof(L));
   L.table_cap = table_cap < 64 ? 64 : table_cap;
   L.pair_cap = pair_capacity(L.table_cap);
-  L.lookback_cap = (unsigned long long)(parts ? parts : 1) * kRadixDigits;
+  L.lookback_cap = radix_scratch_words(parts ? parts : 1);
   L.n_cap = tmp_keys;
   const unsigned long long pc = L.pair_cap;
   unsigned long long o = 0;

@@ -92,7 +92,7 @@ struct Record {
   int path;       // final branch
   int n_tiny;
   int pad0;
-  long long tiny_keys[kTinyMax];  // the u <= 8 distinct sample values, ascending
+  long long tiny_keys[kTinyMax];  // the u <= 8 distinct sample values (first-sample order)
   unsigned long long tiny_mult;   // odd multiplier hashing the tiny keys to distinct
   int tiny_hash_ok;               //   buckets of kTinyBuckets (0: none found)
   int pad_t;
@@ -113,8 +113,9 @@ struct Ctrl {
   unsigned inversion;           // IsMonotone found a descent
   unsigned pad2;
   unsigned long long special;   // keys equal to the type minimum (the empty marker)
-  unsigned long long unused0;
-  unsigned unused_tickets[16];
+  unsigned long long key_or;     // radix (all CTAs): OR of the order-mapped keys
+  unsigned long long key_nor;    //   and OR of their complements (bits that vary)
+  unsigned unused_tickets[14];
   unsigned hist[8][kRadixDigits];  // radix: global digit counts per pass
   unsigned long long chunk_sums[1024];  // scan: per-CTA partial sums
 };
@@ -189,10 +190,18 @@ constexpr unsigned long long pair_capacity(unsigned long long tcap) {
   return tcap / 2 + 2 > (unsigned long long)kSmallPairs ? tcap / 2 + 2 : (unsigned long long)kSmallPairs;
 }
 
-// 64-bit words of the radix scratch: per-CTA digit counts and bases, two
-// [kMaxGrid][kRadixDigits] arrays of 32-bit words (independent of n).
+// 64-bit words of the radix scratch of a scope of `parts` CTAs: per-CTA
+// digit counts and bases, two [parts][kRadixDigits] arrays of 32-bit words,
+// then the grid-wide sampler's kSamples gathered keys in the last kSamples
+// words (apart, because a CTA may start counting digits while another still
+// reads the samples).
+constexpr unsigned long long radix_scratch_words(unsigned long long parts) {
+  return parts * kRadixDigits + (unsigned long long)kSamples;
+}
+
+// The same for any grid up to kMaxGrid (independent of n).
 constexpr unsigned long long lookback_words(unsigned long long /*items*/) {
-  return (unsigned long long)kMaxGrid * kRadixDigits;
+  return radix_scratch_words(kMaxGrid);
 }
 
 // ---------------------------------------------------------------------------

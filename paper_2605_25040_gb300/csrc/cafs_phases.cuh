@@ -1046,10 +1046,72 @@ struct PassSmem {
   unsigned failed;
 };
 
+// Step (a) of a pass over all CTAs: digit `pass` counted over this CTA's
+// range of tiles, stored as the CTA's part counts in the radix scratch and
+// added to the pass's global totals (Ctrl::hist).  With kBits, also the OR of
+// the order-mapped keys and of their complements (the key bits that vary),
+// so that one read of the keys serves pass 0's counts and the choice of
+// passes.  The caller's grid barrier publishes all of it.
+template <typename K, bool kBits>
+__device__ void radix_count(const Params& p, const K* in_k, unsigned long long n, int pass,
+                            unsigned char* smem, const GridScope& sc) {
+  using T = KeyTraits<K>;
+  Ctrl* c = p.ctrl;
+  const int shift = pass * kRadixBits;
+  const unsigned long long ntiles = (n + kRadixTile - 1) / kRadixTile;
+  const unsigned b = sc.part(), nb = sc.nparts();
+  const unsigned long long i0 = (ntiles * b / nb) * kRadixTile;
+  const unsigned long long i1e = (ntiles * (b + 1) / nb) * kRadixTile;
+  const unsigned long long i1 = i1e < n ? i1e : n;
+  unsigned* hist = reinterpret_cast<PassSmem*>(smem)->hist;
+  if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = 0u;
+  __syncthreads();
+  unsigned long long o1 = 0ull, o0 = 0ull;
+  constexpr int U = 4;
+  for (unsigned long long base = i0 + threadIdx.x; base < i1; base += (unsigned long long)U * kThreads) {
+    K kk[U];
+    #pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const unsigned long long i = base + (unsigned long long)j * kThreads;
+      kk[j] = i < i1 ? __ldcg(in_k + i) : (K)0;
+    }
+    #pragma unroll
+    for (int j = 0; j < U; ++j) {
+      if (base + (unsigned long long)j * kThreads < i1) {
+        atomicAdd(hist + radix_digit(kk[j], shift), 1u);
+        if constexpr (kBits) {
+          const typename T::U u = (typename T::U)kk[j] ^ T::kSign;
+          o1 |= (unsigned long long)u;
+          o0 |= (unsigned long long)(typename T::U)~u;
+        }
+      }
+    }
+  }
+  if constexpr (kBits) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      o1 |= __shfl_xor_sync(0xffffffffu, o1, o);
+      o0 |= __shfl_xor_sync(0xffffffffu, o0, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (o1) atomicOr(&c->key_or, o1);
+      if (o0) atomicOr(&c->key_nor, o0);
+    }
+  }
+  unsigned* cta_cnt = reinterpret_cast<unsigned*>(p.lookback);   // [nb][256]
+  __syncthreads();
+  if (threadIdx.x < kRadixDigits) {
+    const unsigned v = hist[threadIdx.x];
+    cta_cnt[b * kRadixDigits + threadIdx.x] = v;
+    if (v) atomicAdd(&c->hist[pass][threadIdx.x], v);
+  }
+}
+
+// `counted`: step (a) of this pass was already done (radix_count).
 template <typename K, bool PAY, class S>
 __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v, K* out_k,
                            unsigned* out_v, unsigned long long n, int pass, unsigned char* smem,
-                           unsigned& epoch, const S& sc) {
+                           unsigned& epoch, const S& sc, bool counted) {
   Ctrl* c = p.ctrl;
   const int shift = pass * kRadixBits;
   const unsigned long long ntiles = (n + kRadixTile - 1) / kRadixTile;
@@ -1081,26 +1143,11 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     const unsigned ex = block_exclusive_scan(v, scratch, &tot);
     if (threadIdx.x < kRadixDigits) running[threadIdx.x] = ex;
   } else {
-    // (a) digit counts of this CTA's range
-    if (threadIdx.x < kRadixDigits) hist[threadIdx.x] = 0u;
-    __syncthreads();
-    {
-      constexpr int U = 4;
-      for (unsigned long long base = i0 + threadIdx.x; base < i1; base += (unsigned long long)U * kThreads) {
-        K kk[U];
-        #pragma unroll
-        for (int j = 0; j < U; ++j) {
-          const unsigned long long i = base + (unsigned long long)j * kThreads;
-          kk[j] = i < i1 ? __ldcg(in_k + i) : (K)0;
-        }
-        #pragma unroll
-        for (int j = 0; j < U; ++j)
-          if (base + (unsigned long long)j * kThreads < i1) atomicAdd(hist + radix_digit(kk[j], shift), 1u);
-      }
+    // (a) digit counts of this CTA's range (and the pass totals)
+    if (!counted) {
+      radix_count<K, false>(p, in_k, n, pass, smem, sc);
+      if (!sc.sync(c, epoch, p.timeout_ns)) return false;
     }
-    __syncthreads();
-    if (threadIdx.x < kRadixDigits) cta_cnt[b * kRadixDigits + threadIdx.x] = hist[threadIdx.x];
-    if (!sc.sync(c, epoch, p.timeout_ns)) return false;
 
     // (b) exclusive scan over CTAs of each digit (this CTA's digits), offset
     // by the digit's global start (exclusive scan of the pass histogram)
@@ -1247,57 +1294,58 @@ __device__ bool radix_sort(const Params& p, const K* src_k, const unsigned* src_
                            const S& sc) {
   using T = KeyTraits<K>;
   constexpr int NP = T::kPasses;
+  constexpr bool kGrid = std::is_same<S, GridScope>::value;
   Ctrl* c = p.ctrl;
-  // Histogram of every digit of every pass (one read of the keys).
-  unsigned* sh = reinterpret_cast<unsigned*>(smem);
-  for (int i = threadIdx.x; i < NP * kRadixDigits; i += blockDim.x) sh[i] = 0u;
-  __syncthreads();
-  {
-    const unsigned long long G = sc.gthreads();
-    const unsigned long long gt = sc.gthread();
-    constexpr int U = 4;
-    for (unsigned long long base = gt; base < n; base += G * U) {
-      K kk[U];
-      #pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const unsigned long long i = base + (unsigned long long)j * G;
-        kk[j] = i < n ? __ldcg(src_k + i) : (K)0;
-      }
-      #pragma unroll
-      for (int j = 0; j < U; ++j) {
-        if (base + (unsigned long long)j * G < n) {
-          const typename T::U u = (typename T::U)kk[j] ^ T::kSign;
-          #pragma unroll
-          for (int q = 0; q < NP; ++q) atomicAdd(sh + q * kRadixDigits + ((u >> (q * kRadixBits)) & 0xFF), 1u);
+  // Plan: a pass whose digit is the same for every key changes nothing.
+  unsigned active_bits = 0;  // pass indices, 4 bits each
+  int na = 0;
+  if constexpr (kGrid) {
+    // Pass 0's counts and the key bits that vary, from one read of the keys;
+    // every later pass counts its own digit (step (a)).
+    radix_count<K, true>(p, src_k, n, 0, smem, sc);
+    if (!sc.sync(c, epoch, p.timeout_ns)) return false;
+    const unsigned long long vary = ld_relaxed_u64(&c->key_or) & ld_relaxed_u64(&c->key_nor);
+    for (int q = 0; q < NP; ++q)
+      if ((vary >> (q * kRadixBits)) & (kRadixDigits - 1)) active_bits |= (unsigned)q << (4 * na++);
+  } else {
+    // One CTA: the histogram of every digit of every pass (one read of the
+    // keys) gives each pass its digit starts directly.
+    unsigned* sh = reinterpret_cast<unsigned*>(smem);
+    for (int i = threadIdx.x; i < NP * kRadixDigits; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    {
+      constexpr int U = 4;
+      for (unsigned long long base = threadIdx.x; base < n; base += (unsigned long long)kThreads * U) {
+        K kk[U];
+        #pragma unroll
+        for (int j = 0; j < U; ++j) {
+          const unsigned long long i = base + (unsigned long long)j * kThreads;
+          kk[j] = i < n ? __ldcg(src_k + i) : (K)0;
+        }
+        #pragma unroll
+        for (int j = 0; j < U; ++j) {
+          if (base + (unsigned long long)j * kThreads < n) {
+            const typename T::U u = (typename T::U)kk[j] ^ T::kSign;
+            #pragma unroll
+            for (int q = 0; q < NP; ++q) atomicAdd(sh + q * kRadixDigits + ((u >> (q * kRadixBits)) & 0xFF), 1u);
+          }
         }
       }
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NP * kRadixDigits; i += blockDim.x)
-    if (sh[i]) atomicAdd(&c->hist[i / kRadixDigits][i % kRadixDigits], sh[i]);
-  if (!sc.sync(c, epoch, p.timeout_ns)) return false;
-
-  // Plan: a pass whose digit is the same for every key changes nothing.
-  int* triv = reinterpret_cast<int*>(smem);  // NP flags
-  int* plan = triv + 8;                      // [0] = count, [1..] = passes
-  if (threadIdx.x < NP) triv[threadIdx.x] = 0;
-  __syncthreads();
-  if (threadIdx.x < kRadixDigits)
+    __syncthreads();
+    for (int i = threadIdx.x; i < NP * kRadixDigits; i += blockDim.x) c->hist[i / kRadixDigits][i % kRadixDigits] = sh[i];
+    __syncthreads();
+    int* triv = reinterpret_cast<int*>(smem);  // NP flags
+    if (threadIdx.x < NP) triv[threadIdx.x] = 0;
+    __syncthreads();
+    if (threadIdx.x < kRadixDigits)
+      for (int q = 0; q < NP; ++q)
+        if ((unsigned long long)c->hist[q][threadIdx.x] == n) triv[q] = 1;
+    __syncthreads();
     for (int q = 0; q < NP; ++q)
-      if ((unsigned long long)ld_relaxed_u32(&c->hist[q][threadIdx.x]) == n) triv[q] = 1;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int na = 0;
-    for (int q = 0; q < NP; ++q)
-      if (!triv[q]) plan[1 + na++] = q;
-    plan[0] = na;
+      if (!triv[q]) active_bits |= (unsigned)q << (4 * na++);
+    __syncthreads();
   }
-  __syncthreads();
-  const int na = plan[0];
-  unsigned active_bits = 0;  // pass indices, 4 bits each
-  for (int a = 0; a < na; ++a) active_bits |= (unsigned)plan[1 + a] << (4 * a);
-  __syncthreads();
   // The last active pass writes dst; earlier ones alternate with tmp.  If the
   // first pass would write over its own input (in-place), every target flips
   // and a final copy tmp -> dst follows.
@@ -1314,7 +1362,8 @@ __device__ bool radix_sort(const Params& p, const K* src_k, const unsigned* src_
     K* ok_ = to_dst ? dst_k : tmp_k;
     unsigned* ov = to_dst ? dst_v : tmp_v;
     const int pass = (int)((active_bits >> (4 * a)) & 15u);
-    if (!radix_pass<K, PAY>(p, cur_k, cur_v, ok_, ov, n, pass, smem, epoch, sc)) return false;
+    if (!radix_pass<K, PAY>(p, cur_k, cur_v, ok_, ov, n, pass, smem, epoch, sc, kGrid && pass == 0))
+      return false;
     if (!sc.sync(c, epoch, p.timeout_ns)) return false;
     cur_k = ok_;
     cur_v = ov;
@@ -1523,7 +1572,7 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
   ring.live = false;
   if (p.mode == kModeSort) ring.start(p, keys, smem, sc);
   if constexpr (kGrid) {
-    long long* gathered = reinterpret_cast<long long*>(p.lookback);
+    long long* gathered = reinterpret_cast<long long*>(p.lookback + (p.lookback_cap - kSamples));
     gather_samples<K>(p, keys, gathered, sc.part(), sc.nparts());
     if (!sc.sync(c, epoch, p.timeout_ns)) { ring.drain(p); return kColumnFailed; }
     phase_sample<K>(p, keys, smem, gathered);
