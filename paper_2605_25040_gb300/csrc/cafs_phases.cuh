@@ -402,7 +402,8 @@ struct Ring {
           const unsigned k = (unsigned)(issued / kRingStages);
           if (!mbar_wait(empty + s, (k - 1) & 1u, p.timeout_ns, c)) { ok = false; break; }
           if (skip) {
-            *reinterpret_cast<volatile unsigned*>(skip_flag) = fl;
+            // set only: a consumer may have raised it already
+            if (fl) *reinterpret_cast<volatile unsigned*>(skip_flag) = 1u;
             fl = ld_relaxed_u32(skip);
           }
           issue(issued);
@@ -483,6 +484,11 @@ struct GlobalTable {
   Ctrl* ctrl;
   unsigned long long C, L;
   int logC;
+  // The CTA's shared copy of the guard (null: none).  Once the guard has
+  // fired the inserts stop at a shared-memory read: every thread of every
+  // CTA probing a small, full table in L2 (the overflow case) queues on the
+  // same few lines, hundreds of microseconds for one column.
+  unsigned* stop;
 };
 
 __device__ __forceinline__ GlobalTable global_table(const Params& p) {
@@ -494,6 +500,7 @@ __device__ __forceinline__ GlobalTable global_table(const Params& p) {
   g.C = p.ctrl->rec.C;
   g.L = p.ctrl->rec.L;
   g.logC = log2_pow2(g.C);
+  g.stop = nullptr;
   return g;
 }
 
@@ -503,7 +510,11 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
   const unsigned long long h = hash_slot(key64, g.logC);
   for (unsigned long long probe = 0; probe < g.C; ++probe) {
     // Once the guard has fired the counts are discarded: stop probing.
-    if ((probe & 3ull) == 3ull && ld_relaxed_u32(&c->overflow)) return;
+    if (g.stop && *reinterpret_cast<volatile unsigned*>(g.stop)) return;
+    if ((probe & 3ull) == 3ull && ld_relaxed_u32(&c->overflow)) {
+      if (g.stop) *reinterpret_cast<volatile unsigned*>(g.stop) = 1u;
+      return;
+    }
     const unsigned long long slot = (h + probe) & mask;
     const unsigned long long k = ld_relaxed_u64(g.keys + slot);
     if (k == key64) {
@@ -516,7 +527,10 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
         const unsigned idx = atomicAdd(&c->occupancy, 1u);
         if (idx < g.C) g.claimed[idx] = (unsigned)slot;
         atomicAdd(g.counts + slot, inc);
-        if (idx >= g.L) atomicExch(&c->overflow, 1u);
+        if (idx >= g.L) {
+          atomicExch(&c->overflow, 1u);
+          if (g.stop) *reinterpret_cast<volatile unsigned*>(g.stop) = 1u;
+        }
         return;
       }
       if (old == key64) {
@@ -526,6 +540,7 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
     }
   }
   atomicExch(&c->overflow, 1u);
+  if (g.stop) *reinterpret_cast<volatile unsigned*>(g.stop) = 1u;
 }
 
 // ---------------------------------------------------------------------------
@@ -804,6 +819,7 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     lt.R = R;
     lt.lane_rep = (threadIdx.x & 31) & (R - 1);
     lt.gt = global_table(p);
+    lt.gt.stop = ring.skip_flag;
     if (tiny_hash) {
       KeyCounter<K, true> kc;
       kc.lt = lt;
@@ -839,7 +855,8 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
   // same keys in the same local slots; each starts at its own offset so
   // that they do not all add to the same global slot at the same time.
   if (use_local) {
-    const GlobalTable g = global_table(p);
+    GlobalTable g = global_table(p);
+    g.stop = ring.skip_flag;
     const int rot = (int)((sc.part() * 977u) & (unsigned)(S - 1));
     for (int i0 = threadIdx.x; i0 < S; i0 += blockDim.x) {
       const int i = (i0 + rot) & (S - 1);
