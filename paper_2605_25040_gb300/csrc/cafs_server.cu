@@ -139,6 +139,71 @@ struct cafs_server {
 namespace cafs {
 namespace {
 
+// One request on an idle server: copy in, the single-column kernel over the
+// grid slot's buffers and the record read on the compute stream, the copy
+// out on the output stream.  The batched launch adds a schedule upload, its
+// own clears, three stages and another cross-stream wait, which at low load
+// only add latency.
+cafs_status enqueue_solo(cafs_server* sv, Request* r, Launch* L) {
+  const BatchBuffers& b = sv->buf;
+  const SlotLayout& gl = b.gl;
+  unsigned char* slot = b.grid_slot;
+  void* d = sv->arena_base + r->off;
+  cudaStream_t s = sv->s_run;
+  if (cudaMemcpyAsync(d, r->host_in, r->bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return CAFS_ERR_CUDA;
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(slot + gl.ctrl);
+  if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+  Params p;
+  std::memset(&p, 0, sizeof(p));
+  p.keys = d;
+  p.out = d;
+  p.n = r->n;
+  p.ctrl = ctrl;
+  p.tkeys = reinterpret_cast<unsigned long long*>(slot + gl.tkeys);
+  p.tcounts = reinterpret_cast<unsigned*>(slot + gl.tcounts);
+  p.claimed = reinterpret_cast<unsigned*>(slot + gl.claimed);
+  p.table_cap = gl.table_cap;
+  p.pkeys_a = slot + gl.pka;
+  p.pvals_a = reinterpret_cast<unsigned*>(slot + gl.pva);
+  p.pkeys_b = slot + gl.pkb;
+  p.pvals_b = reinterpret_cast<unsigned*>(slot + gl.pvb);
+  p.skeys = slot + gl.sk;
+  p.svals = reinterpret_cast<unsigned*>(slot + gl.sv);
+  p.offsets = reinterpret_cast<unsigned*>(slot + gl.off);
+  p.pair_cap = gl.pair_cap;
+  p.tmp = slot + gl.tmp;
+  p.lookback = reinterpret_cast<unsigned long long*>(slot + gl.look);
+  p.lookback_cap = gl.lookback_cap;
+  p.sample_keys = reinterpret_cast<long long*>(slot + gl.sample);
+  p.mode = kModeSort;
+  p.local_slots_max = sv->tuning.local_slots_max;
+  p.replicas_max = sv->tuning.replicas_max;
+  p.emit_tile_vec = sv->tuning.emit_tile_vec;
+  p.timeout_ns = wait_timeout_ns();
+  const int dtype = r->dtype == CAFS_INT64 ? 1 : 0;
+  cudaError_t e;
+  if (r->n < kSmallN) {
+    e = launch_small(p, dtype, s);
+  } else {
+    // the same CTA count rule as the single-column entry point, within the
+    // grid slot's radix scratch (sized for sv->grid CTAs)
+    unsigned long long grid = (r->n + 16383) / 16384;
+    if (grid > (unsigned long long)sv->grid) grid = (unsigned long long)sv->grid;
+    e = launch_pipeline(p, dtype, (int)grid, s);
+  }
+  if (e != cudaSuccess) return CAFS_ERR_CUDA;
+  count_launches(1);
+  std::memset(L->h_state, 0, 2 * sizeof(BatchState));   // no batch state: both key types OK
+  // The copy out goes on its own stream, as in the batched path, so that a
+  // batch formed meanwhile does not wait behind it.
+  if (cudaMemcpyAsync(L->h_records, &ctrl->rec, sizeof(Record), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaEventRecord(sv->ev_run, s) != cudaSuccess || cudaStreamWaitEvent(sv->s_out, sv->ev_run, 0) != cudaSuccess ||
+      cudaMemcpyAsync(r->host_out, d, r->bytes, cudaMemcpyDeviceToHost, sv->s_out) != cudaSuccess ||
+      cudaEventRecord(L->done, sv->s_out) != cudaSuccess)
+    return CAFS_ERR_CUDA;
+  return CAFS_OK;
+}
+
 void scheduler_loop(cafs_server* sv) {
   cudaSetDevice(sv->device);
   Schedule sc;
@@ -146,6 +211,7 @@ void scheduler_loop(cafs_server* sv) {
   for (;;) {
     Launch* L = nullptr;
     std::vector<Request*> batch;
+    bool idle = false;   // nothing in flight when this batch was formed
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       for (;;) {
@@ -165,14 +231,27 @@ void scheduler_loop(cafs_server* sv) {
           if (!batch.empty()) {
             L = sv->free_launches.back();
             sv->free_launches.pop_back();
+            idle = sv->inflight.empty();
             break;
           }
         }
         sv->cv_sched.wait(lk);
       }
     }
-    // Copies in, one batched launch, copies out.
     cafs_status st = CAFS_OK;
+    if (idle && batch.size() == 1) {
+      st = enqueue_solo(sv, batch[0], L);
+      L->reqs.swap(batch);
+      {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (st != CAFS_OK && sv->fatal == CAFS_OK) sv->fatal = st;
+        sv->inflight.push_back(L);
+        sv->launches++;
+      }
+      sv->cv_done.notify_one();
+      continue;
+    }
+    // Copies in, one batched launch, copies out.
     cols.resize(batch.size());
     for (size_t i = 0; i < batch.size(); ++i) {
       Request* r = batch[i];
