@@ -940,8 +940,8 @@ __device__ void phase_rank_pairs(const Params& p, unsigned occ, unsigned long lo
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort, 8-bit digits, stable one-sweep passes with decoupled
-// look-back across tiles of kRadixTile items (all CTAs).
+// LSD radix sort, 8-bit digits, stable reduce-then-scan passes over tiles
+// of kRadixTile items (all CTAs of the scope).
 // ---------------------------------------------------------------------------
 template <typename K>
 __device__ __forceinline__ unsigned radix_digit(K k, int shift) {
