@@ -15,6 +15,10 @@ the paper's steps in the paper's order:
   non-decreasing rearrangement of the input multiset, produced as the paper's
   count-then-emit skeleton (Sec. 4.1): count each distinct key, then emit each
   key ``count`` times in increasing key order.
+* ``stable_argsort`` -- the permutation of Sec. 3.1's problem statement, with
+  equal keys in input order, by the same count-then-emit skeleton: the
+  positions of each distinct key collected in input order, then emitted in
+  increasing key order.
 * ``sample_positions`` / ``chao1`` -- the strided sampler and the smoothed
   Chao1 estimator (Sec. 2.4, Sec. 4.3, Algorithm 2, Eq. 5).
 * ``table_size`` -- the hash-table sizing of Eq. 6 with its clamps (Sec. 4.5).
@@ -106,6 +110,20 @@ def frequency_sort(keys: np.ndarray) -> np.ndarray:
     keys = _check_keys(keys)
     distinct, counts = np.unique(keys, return_counts=True)
     return np.repeat(distinct, counts).astype(keys.dtype, copy=False)
+
+
+def stable_argsort(keys: np.ndarray) -> np.ndarray:
+    """Sec. 3.1's permutation pi (keys[pi] non-decreasing) with equal keys in
+    input order, as count-then-emit (Sec. 4.1) over positions: every distinct
+    key collects the positions where it occurs, in input order; the position
+    lists are then emitted in increasing key order.  Returns uint32 positions.
+    """
+    keys = _check_keys(keys)
+    positions: dict[int, list[int]] = {}
+    for i, k in enumerate(keys.tolist()):
+        positions.setdefault(k, []).append(i)
+    out = [i for k in sorted(positions) for i in positions[k]]
+    return np.asarray(out, dtype=np.uint32)
 
 
 def is_monotone(keys: np.ndarray) -> bool:

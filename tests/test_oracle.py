@@ -73,6 +73,43 @@ def test_frequency_sort_invariants(n, k, dtype):
     assert np.array_equal(O.frequency_sort(G.shuffle(x, 5)), y)
 
 
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_stable_argsort_brute_force_tiny(dtype):
+    # pi by the definition: positions ordered by (key, position), a stable
+    # insertion sort of the positions
+    info = np.iinfo(dtype)
+    alphabet = [info.min, -1, 0, info.max]
+    for length in range(0, 7):
+        for seq in itertools.product(alphabet, repeat=length):
+            arr = np.array(seq, dtype=dtype)
+            pos = list(range(length))
+            for i in range(1, length):
+                v = pos[i]
+                j = i - 1
+                while j >= 0 and seq[pos[j]] > seq[v]:
+                    pos[j + 1] = pos[j]
+                    j -= 1
+                pos[j + 1] = v
+            got = O.stable_argsort(arr)
+            assert got.dtype == np.uint32
+            assert got.tolist() == pos
+
+
+@pytest.mark.parametrize("n,k,dtype", [(5000, 3, np.int32), (20000, 200, np.int64), (30000, 30000, np.int64)])
+def test_stable_argsort_invariants(n, k, dtype):
+    x = G.column(n, k, "zipf", dtype, seed=4)
+    pi = O.stable_argsort(x)
+    # a permutation of the positions
+    assert np.array_equal(np.sort(pi), np.arange(n, dtype=np.uint32))
+    # keys in pi order are the sorted keys
+    assert np.array_equal(x[pi], O.frequency_sort(x))
+    # equal keys keep their input order
+    same = x[pi][1:] == x[pi][:-1]
+    assert bool(np.all(pi[1:][same] > pi[:-1][same]))
+    # a stable library sort agrees
+    assert np.array_equal(pi, np.argsort(x, kind="stable").astype(np.uint32))
+
+
 def test_is_monotone_brute_force():
     for length in range(0, 6):
         for seq in itertools.product([0, 1, 2], repeat=length):
