@@ -126,6 +126,22 @@ cafs_status cafs_sort(const void* keys, size_t n, cafs_dtype dtype, void* out,
 cafs_status cafs_sort_ex(const void* keys, size_t n, cafs_dtype dtype, void* out,
                          cafs_report* report, void* stream);
 
+/* Stable argsort: the permutation pi of Sec. 3.1's problem statement,
+ * x[pi[0]] <= x[pi[1]] <= ... <= x[pi[n-1]], with equal keys in input order.
+ * keys: device pointer, n elements of dtype (not written).
+ * out: device pointer, n elements: receives the sorted keys (the same result
+ *   as cafs_sort).  perm: device pointer, n uint32_t: receives pi.
+ * keys, out and perm must not overlap at all (CAFS_ERR_ALIAS); n <= 2^32-1.
+ * The column takes the path cafs_sort would take (Alg. 3); on the count
+ * paths each key's rank among the K' distinct keys is then sorted stably
+ * with its input position (one LSD radix pass per byte of K'-1), on the
+ * radix paths the (key, position) pairs are; a sorted column gives the
+ * identity.  Asynchronous on `stream` unless `report` is non-NULL (then
+ * blocking, as cafs_sort_ex).  The library keeps 16 bytes per key of extra
+ * scratch for this call in the stream's workspace. */
+cafs_status cafs_argsort(const void* keys, size_t n, cafs_dtype dtype, void* out, uint32_t* perm,
+                         cafs_report* report, void* stream);
+
 /* Sampler + Chao1 + dispatcher only (Alg. 2 and Alg. 3, Eq. 5-6): fills *est
  * (host memory).  Blocking: waits for `stream`.  The IsMonotone test of
  * Alg. 3 is a full scan on the device, run only when the samples ascend. */

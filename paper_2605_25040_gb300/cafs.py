@@ -114,6 +114,8 @@ SIGNATURES = {
                                     ctypes.POINTER(Report), ctypes.c_void_p]),
     "cafs_estimate_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                        ctypes.POINTER(Estimate), ctypes.c_void_p]),
+    "cafs_argsort": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
     "cafs_sort_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                       ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
     "cafs_sort_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
@@ -231,6 +233,32 @@ def sort_ex(keys, out=None, stream=None):
                                 out.data_ptr(), ctypes.byref(rep), _stream_handle(stream)),
                "cafs_sort_ex")
     return out, rep.as_dict()
+
+
+def argsort(keys, out=None, perm=None, stream=None, report: bool = False):
+    """Stable argsort of a 1-D int32/int64 CUDA tensor: returns (sorted keys,
+    perm) with keys[perm] == sorted keys and equal keys in input order
+    (perm is int32 holding the uint32 positions); with ``report`` also the
+    report dict (then the call waits for the stream)."""
+    import torch
+    lib = load()
+    keys = _device_tensor(keys)
+    if out is None:
+        out = torch.empty_like(keys)
+    if perm is None:
+        perm = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+    if out.dtype != keys.dtype or out.numel() != keys.numel() or not out.is_contiguous():
+        raise ValueError("out must match keys in dtype and size")
+    if perm.dtype != torch.int32 or perm.numel() != keys.numel() or not perm.is_contiguous():
+        raise ValueError("perm must be a contiguous int32 tensor of keys' size")
+    rep = Report() if report else None
+    with torch.cuda.device(keys.device):
+        _check(lib.cafs_argsort(keys.data_ptr(), keys.numel(), _dtype_code(keys.dtype), out.data_ptr(),
+                                perm.data_ptr(), ctypes.byref(rep) if report else None,
+                                _stream_handle(stream)), "cafs_argsort")
+    if report:
+        return out, perm, rep.as_dict()
+    return out, perm
 
 
 def estimate_k(keys, stream=None) -> dict:

@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "cafs.h"
+#include "cafs_argsort.h"
 #include "cafs_internal.h"
 
 namespace cafs {
@@ -24,6 +25,7 @@ struct DeviceInfo {
   bool ready = false;
   int sms = 0;
   int max_grid[2] = {0, 0};
+  int max_grid_arg[2] = {0, 0};   // argsort kernels
 };
 std::map<int, DeviceInfo> g_dev;
 
@@ -50,6 +52,8 @@ struct Workspace {
   unsigned long long* lookback = nullptr;
   long long* sample_keys = nullptr;
   void* io = nullptr;
+  unsigned* arg = nullptr;     // argsort scratch: 4 arrays of arg_n words
+  unsigned long long arg_n = 0;
   Record* host_rec = nullptr;  // pinned
 };
 std::map<std::pair<int, uintptr_t>, Workspace*> g_ws;
@@ -64,14 +68,15 @@ void release_buffers(Workspace* w) {
   free_dev(w->ctrl); free_dev(w->tkeys); free_dev(w->tcounts); free_dev(w->claimed);
   free_dev(w->pkeys_a); free_dev(w->pvals_a); free_dev(w->pkeys_b); free_dev(w->pvals_b);
   free_dev(w->skeys); free_dev(w->svals); free_dev(w->offsets); free_dev(w->tmp);
-  free_dev(w->lookback); free_dev(w->sample_keys);
+  free_dev(w->lookback); free_dev(w->sample_keys); free_dev(w->arg);
+  w->arg_n = 0;
   w->n_cap = 0; w->tmp_bytes = 0; w->table_cap = 0; w->pair_cap = 0; w->lookback_cap = 0;
 }
 
 cafs_status ensure_device(int dev, DeviceInfo** out) {
   DeviceInfo& d = g_dev[dev];
   if (!d.ready) {
-    if (prepare_kernels() != cudaSuccess) return CAFS_ERR_CUDA;
+    if (prepare_kernels() != cudaSuccess || prepare_argsort_kernels() != cudaSuccess) return CAFS_ERR_CUDA;
     if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CAFS_ERR_CUDA;
     for (int t = 0; t < 2; ++t) {
       int bps = 0;
@@ -79,6 +84,9 @@ cafs_status ensure_device(int dev, DeviceInfo** out) {
       long long g = (long long)bps * d.sms;
       if (g > 1024) g = 1024;  // Ctrl::chunk_sums holds one partial sum per CTA
       d.max_grid[t] = (int)g;
+      if (argsort_occupancy(t, &bps) != cudaSuccess || bps < 1) return CAFS_ERR_CUDA;
+      g = (long long)bps * d.sms;
+      d.max_grid_arg[t] = (int)(g > 1024 ? 1024 : g);
     }
     d.ready = true;
   }
@@ -196,10 +204,8 @@ void fill_estimate(const Record& r, cafs_estimate* e) {
   e->dispatch = (cafs_path)r.dispatch;
 }
 
-// Enqueues one pipeline run on stream s (g_mu held).
-cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* out,
-                    unsigned long long n, int dtype, int mode, cudaStream_t s) {
-  if (cudaMemsetAsync(w->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+// Kernel parameters of one column over workspace w (g_mu held).
+Params pipeline_params(Workspace* w, const void* keys, void* out, unsigned long long n, int mode) {
   Params p;
   std::memset(&p, 0, sizeof(p));
   p.keys = keys;
@@ -226,14 +232,27 @@ cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* o
   p.replicas_max = kDefaultReplicasMax;
   p.emit_tile_vec = kEmitTileVecDefault;
   p.timeout_ns = g_timeout_ns;
+  return p;
+}
+
+// CTAs of a cooperative launch over n keys: one per 16384 keys, at most
+// one per SM (the persistent kernels' occupancy).
+int launch_grid(unsigned long long n, int max_grid) {
+  long long grid = (long long)((n + 16383) / 16384);
+  if (grid > max_grid) grid = max_grid;
+  return grid < 1 ? 1 : (int)grid;
+}
+
+// Enqueues one pipeline run on stream s (g_mu held).
+cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* out,
+                    unsigned long long n, int dtype, int mode, cudaStream_t s) {
+  if (cudaMemsetAsync(w->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+  const Params p = pipeline_params(w, keys, out, n, mode);
   cudaError_t e;
   if (n < kSmallN) {
     e = launch_small(p, dtype, s);
   } else {
-    long long grid = (long long)((n + 16383) / 16384);
-    if (grid > d->max_grid[dtype]) grid = d->max_grid[dtype];
-    if (grid < 1) grid = 1;
-    e = launch_pipeline(p, dtype, (int)grid, s);
+    e = launch_pipeline(p, dtype, launch_grid(n, d->max_grid[dtype]), s);
   }
   if (e != cudaSuccess) return CAFS_ERR_CUDA;
   g_launches++;
@@ -286,6 +305,68 @@ cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, c
   return CAFS_OK;
 }
 
+// Stable argsort of one column (keys, out and perm pairwise disjoint).
+cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, uint32_t* perm,
+                         cafs_report* report, void* stream) {
+  cafs_status st = check_args_impl(keys, n, dtype, out, true);
+  if (st != CAFS_OK) return st;
+  if (n == 0) {
+    if (report) {
+      std::memset(report, 0, sizeof(*report));
+      report->path = CAFS_PATH_EMPTY;
+      report->est.dispatch = CAFS_PATH_EMPTY;
+    }
+    return CAFS_OK;
+  }
+  if (!perm || reinterpret_cast<uintptr_t>(perm) % 4) return CAFS_ERR_INVALID_ARGUMENT;
+  const uintptr_t kb = dtype == CAFS_INT64 ? 8 : 4;
+  const uintptr_t k0 = reinterpret_cast<uintptr_t>(keys), o0 = reinterpret_cast<uintptr_t>(out);
+  const uintptr_t p0 = reinterpret_cast<uintptr_t>(perm);
+  const uintptr_t kbytes = (uintptr_t)n * kb, pbytes = (uintptr_t)n * 4;
+  auto overlap = [](uintptr_t a, uintptr_t an, uintptr_t b, uintptr_t bn) { return a < b + bn && b < a + an; };
+  if (overlap(k0, kbytes, o0, kbytes) || overlap(p0, pbytes, k0, kbytes) || overlap(p0, pbytes, o0, kbytes))
+    return CAFS_ERR_ALIAS;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CAFS_ERR_CUDA;
+  DeviceInfo* d = nullptr;
+  if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
+  Workspace* w = workspace_for(dev, s);
+  if ((st = ensure_workspace(w, n, dtype, s, false)) != CAFS_OK) return st;
+  if ((unsigned long long)n > w->arg_n) {
+    if (w->arg) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return CAFS_ERR_CUDA;
+      free_dev(w->arg);
+      w->arg_n = 0;
+    }
+    if (alloc(&w->arg, (size_t)n * 16) != cudaSuccess) {
+      cudaGetLastError();
+      return CAFS_ERR_OUT_OF_MEMORY;
+    }
+    w->arg_n = n;
+  }
+  if (cudaMemsetAsync(w->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+  ArgsortParams ap;
+  ap.p = pipeline_params(w, keys, out, n, kModeSort);
+  ap.perm = perm;
+  ap.rk = w->arg;
+  ap.iv = w->arg + n;
+  ap.tv = w->arg + 2 * (size_t)n;
+  ap.rk2 = w->arg + 3 * (size_t)n;
+  cudaError_t e;
+  if (n < kSmallN) e = launch_small_argsort(ap, dtype, s);
+  else e = launch_argsort(ap, dtype, launch_grid(n, d->max_grid_arg[dtype]), s);
+  if (e != cudaSuccess) return CAFS_ERR_CUDA;
+  g_launches++;
+  if (report) {
+    Record r;
+    if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
+    fill_report_impl(r, report);
+  }
+  return CAFS_OK;
+}
+
 }  // namespace
 
 void count_launches(unsigned k) { g_launches += k; }
@@ -311,6 +392,11 @@ cafs_status cafs_sort(const void* keys, size_t n, cafs_dtype dtype, void* out, v
 cafs_status cafs_sort_ex(const void* keys, size_t n, cafs_dtype dtype, void* out,
                          cafs_report* report, void* stream) {
   return sort_impl(keys, n, dtype, out, report, stream);
+}
+
+cafs_status cafs_argsort(const void* keys, size_t n, cafs_dtype dtype, void* out, uint32_t* perm,
+                         cafs_report* report, void* stream) {
+  return argsort_impl(keys, n, dtype, out, perm, report, stream);
 }
 
 cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype, cafs_estimate* est,

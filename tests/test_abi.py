@@ -61,6 +61,24 @@ def test_argument_errors_are_synchronous(lib):
     assert lib.cafs_estimate_k(p, 4, cafs.INT64, None, None) == 1
 
 
+def test_argsort_argument_errors_are_synchronous(lib):
+    buf = (ctypes.c_int64 * 64)()
+    p = ctypes.addressof(buf)
+    # n == 0: a no-op with NULL pointers
+    assert lib.cafs_argsort(None, 0, cafs.INT64, None, None, None, None) == 0
+    assert lib.cafs_argsort(p, 4, 6, p + 64, p + 128, None, None) == 2
+    assert lib.cafs_argsort(p, 1 << 32, cafs.INT64, p + 64, p + 128, None, None) == 3
+    # NULL out or perm, misaligned perm
+    assert lib.cafs_argsort(p, 4, cafs.INT64, None, p + 128, None, None) == 1
+    assert lib.cafs_argsort(p, 4, cafs.INT64, p + 64, None, None, None) == 1
+    assert lib.cafs_argsort(p, 4, cafs.INT64, p + 64, p + 130, None, None) == 1
+    # keys, out and perm must be pairwise disjoint (keys == out too)
+    assert lib.cafs_argsort(p, 4, cafs.INT64, p, p + 128, None, None) == 4
+    assert lib.cafs_argsort(p, 4, cafs.INT64, p + 64, p + 16, None, None) == 4
+    assert lib.cafs_argsort(p, 4, cafs.INT64, p + 64, p + 80, None, None) == 4
+    assert lib.cafs_argsort(p, 4, cafs.INT32, p + 64, p + 72, None, None) == 4
+
+
 def test_names(lib):
     assert lib.cafs_status_string(0) == b"ok"
     assert lib.cafs_path_string(4) == b"main"
