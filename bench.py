@@ -13,11 +13,15 @@ Printed JSON line (rank 0): value = whole-job Gkeys/s; roofline = the
 pipeline kernel's achieved bytes (one read + one write of every column, the
 sort's minimum traffic) per CUDA-event second against the measured HBM copy
 bandwidth, with the DRAM traffic of the committed ncu summary when it was
-taken on the current kernel sources; e2e = the same metric through
-cafs_sort_host with pinned host buffers (copies inside the timed region);
+taken on the current kernel sources; e2e = the same metric through the
+request server (cafs_server_run_trace) with pinned host buffers, copies
+inside the timed region, copies and sorting of different columns overlapped
+(the blocking one-column-at-a-time cafs_sort_host figure beside it);
 cpu_baseline = the CPU oracle on a bounded sample of the same columns.
 
-Two more legs (rank 0; --no-batched / --no-served skip them):
+Three more legs (rank 0; --no-argsort / --no-batched / --no-served skip them):
+  argsort: cafs_argsort (sorted keys plus the stable permutation) on four
+    sweep columns, checked against and timed beside torch.sort(stable=True);
   batched: 4096 int64 columns (N log-uniform [1e3, 1e6], K log-uniform
     [2, min(N/4, 5e4)], Zipf 1.1) and 64 mixed int32/int64 columns (N 1e3..3e7,
     K 2..N, 4 spill-trigger columns): one recorded batched launch (default
@@ -245,6 +249,36 @@ def _batched_case(torch, cafs, keys, workload, tune=True):
     }
 
 
+def bench_argsort(torch, cafs, dev_in, names, peak, want=("uniform_K4", "uniform_K200", "zipf_K4096",
+                                                        "uniform_K30000000")):
+    """cafs_argsort (sorted keys + stable permutation) on some sweep columns,
+    checked against torch's stable sort; torch.sort(stable=True) timed beside."""
+    res = {"timing": "CUDA events on the current stream, median of 5 after 2 warm-ups; inputs larger than L2",
+           "algorithmic_bytes_per_key": 20, "columns": []}
+    ok_all = True
+    for name, x in zip(names, dev_in):
+        if name not in want:
+            continue
+        out = torch.empty_like(x)
+        perm = torch.empty(x.numel(), dtype=torch.int32, device=x.device)
+        ms, ms_min = _time_ms(torch, lambda: cafs.argsort(x, out, perm))
+        ref = torch.sort(x, stable=True)
+        ok = bool(torch.equal(ref.values, out)) and bool(torch.equal(ref.indices, perm.long() & 0xFFFFFFFF))
+        ok_all &= ok
+        del ref
+        t_ms, _ = _time_ms(torch, lambda: torch.sort(x, stable=True))
+        _, _, r = cafs.argsort(x, out, perm, report=True)
+        n = x.numel()
+        res["columns"].append({"column": name, "path": cafs.path_name(r["path"]), "ms": round(ms, 4),
+                               "gkeys_s": round(n / (ms / 1e3) / 1e9, 2),
+                               "frac_hbm": round(20 * n / (ms / 1e3) / 1e9 / peak, 4),
+                               "torch_sort_stable_ms": round(t_ms, 4)})
+        del out, perm
+    res["verified_vs_torch_sort_stable"] = ok_all
+    torch.cuda.empty_cache()
+    return res
+
+
 def bench_batched(torch, cafs):
     from paper_2605_25040_gb300 import datagen as G
     res = {}
@@ -363,6 +397,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-form measurement")
+    ap.add_argument("--no-argsort", action="store_true", help="skip the argsort measurement")
     ap.add_argument("--columns", default="",
                     help="comma-separated subset of sweep columns (e.g. uniform_K200); default all")
     args = ap.parse_args()
@@ -510,6 +545,10 @@ def main():
                "blocking_per_column": {"value": n * ncol * e2e_steps * world / dt_blocking / 1e9,
                                        "api": "cafs_sort_host, one column at a time"}}
 
+    argsort = None
+    if rank == 0 and not args.no_argsort:
+        argsort = bench_argsort(torch, cafs, dev_in, names, peak)
+
     batched = served = None
     if rank == 0 and not args.no_batched:
         del dev_out
@@ -558,6 +597,7 @@ def main():
         "sweep": sweep,
         "batched": batched,
         "served": served,
+        "argsort": argsort,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
