@@ -325,6 +325,17 @@ cafs_status cafs_serial_run_trace(const cafs_request* reqs, size_t nreq, const d
                                   double* latency_us, cafs_report* reports, double* elapsed_s,
                                   void* stream);
 
+/* Hash seed (SURVEY's randomised-seed row; Eq. 4 fixes the golden-ratio
+ * multiplier).  seed == 0 (the default): every table hash uses the
+ * golden-ratio constants.  seed != 0: every later call (each sort, argsort,
+ * batch launch or plan, server launch) draws its own odd 64-bit Eq. 4
+ * multiplier and odd 32-bit shared-table multiplier from the seed and a
+ * process-wide call counter (SplitMix64), so that no fixed key set collides
+ * in every call.  Which slot a key lands in never changes a count, a result,
+ * a path or a report field; only the speed of adversarial inputs changes.
+ * Setting a seed restarts the call counter. */
+void cafs_set_hash_seed(uint64_t seed);
+
 /* Testing hooks (no counterpart in the paper).  `flags` bit 0 makes CTA 0 of
  * the next pipeline launches skip the first grid barrier, so that the other
  * CTAs' bounded wait runs out and the launch reports CAFS_ERR_TIMEOUT in

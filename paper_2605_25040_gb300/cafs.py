@@ -116,6 +116,7 @@ SIGNATURES = {
                                        ctypes.POINTER(Estimate), ctypes.c_void_p]),
     "cafs_argsort": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
+    "cafs_set_hash_seed": (None, [ctypes.c_uint64]),
     "cafs_sort_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                       ctypes.c_void_p, ctypes.POINTER(Report), ctypes.c_void_p]),
     "cafs_sort_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
@@ -259,6 +260,12 @@ def argsort(keys, out=None, perm=None, stream=None, report: bool = False):
     if report:
         return out, perm, rep.as_dict()
     return out, perm
+
+
+def set_hash_seed(seed: int) -> None:
+    """0: golden-ratio table hashes (default); else each later call draws its
+    own odd multipliers from the seed (never changes a result or a path)."""
+    load().cafs_set_hash_seed(int(seed) & 0xFFFFFFFFFFFFFFFF)
 
 
 def estimate_k(keys, stream=None) -> dict:

@@ -17,6 +17,28 @@ namespace cafs {
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
+uint64_t g_hash_seed = 0;        // 0: the golden-ratio multipliers
+uint64_t g_hash_calls = 0;
+
+// SplitMix64 (Steele, Lea, Flood 2014) finaliser: draws the multipliers.
+uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// g_mu held.
+void next_hash_multipliers_locked(unsigned long long* hash_mult, unsigned* local_mult) {
+  if (g_hash_seed == 0) {
+    *hash_mult = 0;
+    *local_mult = 0;
+    return;
+  }
+  const uint64_t a = mix64(g_hash_seed ^ mix64(++g_hash_calls));
+  *hash_mult = a | 1ull;
+  *local_mult = (unsigned)(mix64(a) >> 32) | 1u;
+}
 std::mutex g_mu;
 unsigned g_test_flags = 0;
 unsigned long long g_timeout_ns = 1000000000ull;  // bounded device waits: 1 s
@@ -232,6 +254,7 @@ Params pipeline_params(Workspace* w, const void* keys, void* out, unsigned long 
   p.replicas_max = kDefaultReplicasMax;
   p.emit_tile_vec = kEmitTileVecDefault;
   p.timeout_ns = g_timeout_ns;
+  next_hash_multipliers_locked(&p.hash_mult, &p.local_mult);
   return p;
 }
 
@@ -370,6 +393,10 @@ cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out
 }  // namespace
 
 void count_launches(unsigned k) { g_launches += k; }
+void next_hash_multipliers(unsigned long long* hash_mult, unsigned* local_mult) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  next_hash_multipliers_locked(hash_mult, local_mult);
+}
 unsigned long long wait_timeout_ns() {
   std::lock_guard<std::mutex> lock(g_mu);
   return g_timeout_ns;
@@ -453,6 +480,12 @@ cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype, vo
   if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
   if (report) fill_report_impl(r, report);
   return CAFS_OK;
+}
+
+void cafs_set_hash_seed(uint64_t seed) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_hash_seed = seed;
+  g_hash_calls = 0;
 }
 
 void cafs_set_test_hooks(uint32_t flags, uint64_t wait_timeout_ns) {

@@ -58,8 +58,9 @@ __device__ __forceinline__ Params column_params(const BatchColumn& col, unsigned
   p.local_slots_max = bp.local_slots_max;
   p.replicas_max = bp.replicas_max;
   p.emit_tile_vec = bp.emit_tile_vec;
-  p.pad_knobs = 0;
+  p.local_mult = bp.local_mult;
   p.timeout_ns = bp.timeout_ns;
+  p.hash_mult = bp.hash_mult;
   return p;
 }
 
@@ -569,6 +570,7 @@ BatchParams make_params(const BatchBuffers* b, const Schedule& sc, const Tuning&
   bp.replicas_max = t.replicas_max;
   bp.emit_tile_vec = t.emit_tile_vec;
   bp.timeout_ns = wait_timeout_ns();
+  next_hash_multipliers(&bp.hash_mult, &bp.local_mult);
   return bp;
 }
 

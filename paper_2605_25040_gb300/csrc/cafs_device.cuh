@@ -40,6 +40,12 @@ constexpr unsigned long long kEmpty64 = 0x8000000000000000ull;
 __device__ __forceinline__ unsigned long long hash_slot(unsigned long long x, int log2size) {
   return log2size == 0 ? 0ull : ((x * kPhi) >> (64 - log2size));
 }
+// Eq. 4 with another odd multiplier (a per-call hash seed; which slot a key
+// lands in never changes a count, the result or the path).
+__device__ __forceinline__ unsigned long long hash_slot_m(unsigned long long x, unsigned long long mult,
+                                                          int log2size) {
+  return log2size == 0 ? 0ull : ((x * mult) >> (64 - log2size));
+}
 
 // Bucket index in a per-CTA shared table of 2^log2size buckets: a 32-bit
 // multiplicative hash of the key folded to 32 bits (the same golden-ratio
@@ -47,6 +53,9 @@ __device__ __forceinline__ unsigned long long hash_slot(unsigned long long x, in
 // changes a count; a 32-bit product costs a third of Eq. 4's 64-bit one.
 __device__ __forceinline__ unsigned local_bucket(unsigned x32, int log2size) {
   return (x32 * 0x9E3779B1u) >> (32 - log2size);
+}
+__device__ __forceinline__ unsigned local_bucket_m(unsigned x32, unsigned mult, int log2size) {
+  return (x32 * mult) >> (32 - log2size);
 }
 __device__ __forceinline__ unsigned fold32(unsigned long long x) { return (unsigned)x ^ (unsigned)(x >> 32); }
 __device__ __forceinline__ unsigned fold32(unsigned x) { return x; }

@@ -151,8 +151,12 @@ struct Params {
   unsigned local_slots_max;
   unsigned replicas_max;
   unsigned emit_tile_vec;
-  unsigned pad_knobs;
+  // Odd multipliers of the per-CTA shared table's bucket hash and of the
+  // global table's Eq. 4 hash (0: the golden-ratio constants).  A per-call
+  // seed draws them; no count, result or path depends on them.
+  unsigned local_mult;
   unsigned long long timeout_ns;
+  unsigned long long hash_mult;
 };
 
 // Default scheduling knobs.
@@ -251,8 +255,9 @@ struct BatchParams {
   SlotLayout cta_layout;
   unsigned n_grid, n_cta;
   unsigned long long defer_min_n;
-  unsigned local_slots_max, replicas_max, emit_tile_vec, pad;
+  unsigned local_slots_max, replicas_max, emit_tile_vec, local_mult;
   unsigned long long timeout_ns;
+  unsigned long long hash_mult;
 };
 
 // Slot layout: a hash table of table_cap slots (with pair arrays for its
@@ -277,6 +282,10 @@ cudaError_t launch_batch(const BatchParams& bp, int dtype, int grid, cudaStream_
 
 // Shared by the host entry points (defined in cafs_api.cu).
 void count_launches(unsigned k);
+// The hash multipliers of the next call: both 0 (the golden-ratio constants)
+// unless a seed was set (cafs_set_hash_seed), then odd values drawn from the
+// seed and a per-process call counter.
+void next_hash_multipliers(unsigned long long* hash_mult, unsigned* local_mult);
 unsigned long long wait_timeout_ns();
 cafs_status check_args(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out);
 void fill_report(const Record& r, cafs_report* rep);

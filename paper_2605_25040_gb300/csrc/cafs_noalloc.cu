@@ -145,6 +145,7 @@ extern "C" cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype 
   p.replicas_max = kDefaultReplicasMax;
   p.emit_tile_vec = kEmitTileVecDefault;
   p.timeout_ns = 1000000000ull;
+  next_hash_multipliers(&p.hash_mult, &p.local_mult);
 
   // The array keeps the previous call's contents: the control block must
   // start at zero and the hash table empty (every key slot the empty marker,

@@ -484,6 +484,7 @@ struct GlobalTable {
   Ctrl* ctrl;
   unsigned long long C, L;
   int logC;
+  unsigned long long mult;   // Eq. 4 multiplier (odd)
   // The CTA's shared copy of the guard (null: none).  Once the guard has
   // fired the inserts stop at a shared-memory read: every thread of every
   // CTA probing a small, full table in L2 (the overflow case) queues on the
@@ -500,6 +501,7 @@ __device__ __forceinline__ GlobalTable global_table(const Params& p) {
   g.C = p.ctrl->rec.C;
   g.L = p.ctrl->rec.L;
   g.logC = log2_pow2(g.C);
+  g.mult = p.hash_mult ? (p.hash_mult | 1ull) : kPhi;
   g.stop = nullptr;
   return g;
 }
@@ -507,7 +509,7 @@ __device__ __forceinline__ GlobalTable global_table(const Params& p) {
 static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long long key64, unsigned inc) {
   Ctrl* c = g.ctrl;
   const unsigned long long mask = g.C - 1;
-  const unsigned long long h = hash_slot(key64, g.logC);
+  const unsigned long long h = hash_slot_m(key64, g.mult, g.logC);
   for (unsigned long long probe = 0; probe < g.C; ++probe) {
     // Once the guard has fired the counts are discarded: stop probing.
     if (g.stop && *reinterpret_cast<volatile unsigned*>(g.stop)) return;
@@ -564,10 +566,11 @@ struct LocalTable {
   unsigned* occ;    // distinct keys held
   unsigned limit;   // at most this many distinct keys (half the slots)
   int logNB, NB, R, lane_rep;
+  unsigned mult;    // bucket-hash multiplier (odd)
   GlobalTable gt;
 
   __device__ __forceinline__ unsigned home(K x) const {
-    return local_bucket(fold32((typename KeyTraits<K>::U)x), logNB);
+    return local_bucket_m(fold32((typename KeyTraits<K>::U)x), mult, logNB);
   }
   __device__ __forceinline__ void add(unsigned slot) const {
     atomicAdd(cnt + slot * R + lane_rep, 1u);
@@ -799,6 +802,7 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     seed.logNB = log2_pow2(S / LocalTable<K>::kBucketSlots);
     seed.R = R;
     seed.lane_rep = 0;
+    seed.mult = p.local_mult ? (p.local_mult | 1u) : 0x9E3779B1u;
     seed.gt = global_table(p);
     const int u = (int)r.u;
     for (int j = threadIdx.x; j < u; j += blockDim.x) {
@@ -818,6 +822,7 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     lt.logNB = log2_pow2(S / LocalTable<K>::kBucketSlots);
     lt.R = R;
     lt.lane_rep = (threadIdx.x & 31) & (R - 1);
+    lt.mult = p.local_mult ? (p.local_mult | 1u) : 0x9E3779B1u;
     lt.gt = global_table(p);
     lt.gt.stop = ring.skip_flag;
     if (tiny_hash) {

@@ -180,6 +180,7 @@ cafs_status enqueue_solo(cafs_server* sv, Request* r, Launch* L) {
   p.replicas_max = sv->tuning.replicas_max;
   p.emit_tile_vec = sv->tuning.emit_tile_vec;
   p.timeout_ns = wait_timeout_ns();
+  next_hash_multipliers(&p.hash_mult, &p.local_mult);
   const int dtype = r->dtype == CAFS_INT64 ? 1 : 0;
   cudaError_t e;
   if (r->n < kSmallN) {
