@@ -19,6 +19,13 @@ the paper's steps in the paper's order:
   equal keys in input order, by the same count-then-emit skeleton: the
   positions of each distinct key collected in input order, then emitted in
   increasing key order.
+* ``ordered_signed`` / ``frequency_sort_any`` / ``final_path_any`` /
+  ``stable_argsort_any`` -- more key types: unsigned integers in their natural
+  order and IEEE-754 binary32/binary64 in the standard's totalOrder (negative
+  NaNs, -inf, negative numbers, -0, +0, positive numbers, +inf, positive
+  NaNs; equal keys are equal bit patterns).  Each maps onto the signed
+  integers of its width by an order-preserving bijection, and the signed
+  functions do the rest.
 * ``sample_positions`` / ``chao1`` -- the strided sampler and the smoothed
   Chao1 estimator (Sec. 2.4, Sec. 4.3, Algorithm 2, Eq. 5).
 * ``table_size`` -- the hash-table sizing of Eq. 6 with its clamps (Sec. 4.5).
@@ -124,6 +131,61 @@ def stable_argsort(keys: np.ndarray) -> np.ndarray:
         positions.setdefault(k, []).append(i)
     out = [i for k in sorted(positions) for i in positions[k]]
     return np.asarray(out, dtype=np.uint32)
+
+
+# More key types: the order each one sorts in, as signed integers of the
+# same width (an order- and equality-preserving bijection).
+_SIGNED_OF = {np.dtype(np.uint32): np.int32, np.dtype(np.uint64): np.int64,
+              np.dtype(np.float32): np.int32, np.dtype(np.float64): np.int64,
+              np.dtype(np.int32): np.int32, np.dtype(np.int64): np.int64}
+
+
+def ordered_signed(keys: np.ndarray) -> np.ndarray:
+    """Signed integers ordered like ``keys``: unsigned keys with the sign bit
+    flipped (0 becomes the signed minimum); IEEE floats by their bits, with
+    the magnitude bits of negative values inverted (a larger magnitude is a
+    smaller number), which is the totalOrder of IEEE 754."""
+    keys = np.asarray(keys)
+    if keys.dtype not in _SIGNED_OF:
+        raise TypeError("unsupported key type")
+    it = _SIGNED_OF[keys.dtype]
+    if keys.dtype.kind == "i":
+        return keys
+    bits = keys.view(it)
+    sign = np.array(np.iinfo(it).min, dtype=it)
+    if keys.dtype.kind == "u":
+        return bits ^ sign
+    return np.where(bits < 0, bits ^ ~sign, bits).astype(it)
+
+
+def from_ordered_signed(ordered: np.ndarray, dtype) -> np.ndarray:
+    """Inverse of ``ordered_signed`` (both maps are their own inverse on the
+    bits)."""
+    dtype = np.dtype(dtype)
+    if dtype.kind == "i":
+        return ordered.astype(dtype, copy=False)
+    it = _SIGNED_OF[dtype]
+    sign = np.array(np.iinfo(it).min, dtype=it)
+    if dtype.kind == "u":
+        return (ordered ^ sign).view(dtype)
+    return np.where(ordered < 0, ordered ^ ~sign, ordered).astype(it).view(dtype)
+
+
+def frequency_sort_any(keys: np.ndarray) -> np.ndarray:
+    """``frequency_sort`` for any supported key type."""
+    keys = np.asarray(keys)
+    return from_ordered_signed(frequency_sort(ordered_signed(keys)), keys.dtype)
+
+
+def final_path_any(keys: np.ndarray) -> int:
+    """``final_path`` for any supported key type (the dispatcher sees the keys
+    in their order; distinct bit patterns are distinct keys)."""
+    return final_path(ordered_signed(keys))
+
+
+def stable_argsort_any(keys: np.ndarray) -> np.ndarray:
+    """``stable_argsort`` for any supported key type."""
+    return stable_argsort(ordered_signed(keys))
 
 
 def is_monotone(keys: np.ndarray) -> bool:

@@ -110,6 +110,62 @@ def test_stable_argsort_invariants(n, k, dtype):
     assert np.array_equal(pi, np.argsort(x, kind="stable").astype(np.uint32))
 
 
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_unsigned_brute_force_tiny(dtype):
+    # natural unsigned order of Python integers
+    w = np.dtype(dtype).itemsize * 8
+    alphabet = [0, 1, 1 << (w - 1), (1 << w) - 1]
+    for length in range(0, 6):
+        for seq in itertools.product(alphabet, repeat=length):
+            arr = np.array(seq, dtype=dtype)
+            got = O.frequency_sort_any(arr)
+            assert got.dtype == arr.dtype
+            assert [int(v) for v in got] == sorted(seq)
+
+
+def _total_order_key(bits: int, w: int):
+    # IEEE 754 totalOrder from its definition: negatives (sign 1) before
+    # positives, larger magnitude (exponent, then significand) first among
+    # negatives and last among positives; NaNs sit beyond the infinities.
+    mag = bits & ((1 << (w - 1)) - 1)
+    return (0, -mag) if bits >> (w - 1) else (1, mag)
+
+
+@pytest.mark.parametrize("fdt,idt", [(np.float32, np.uint32), (np.float64, np.uint64)])
+def test_float_total_order_brute_force_tiny(fdt, idt):
+    w = np.dtype(fdt).itemsize * 8
+    specials = np.array([np.nan, -np.inf, -1.5, -0.0, 0.0, 2.0 ** -1030 if w == 64 else 2.0 ** -140, np.inf],
+                        dtype=fdt)
+    bits = [int(b) for b in specials.view(idt)]
+    bits.append(bits[0] | (1 << (w - 1)))       # a negative NaN
+    bits.append(bits[0] | 1)                    # a NaN with another payload
+    for length in range(0, 5):
+        for seq in itertools.product(bits, repeat=length):
+            arr = np.array(seq, dtype=idt).view(fdt)
+            got = [int(b) for b in O.frequency_sort_any(arr).view(idt)]
+            assert got == sorted(seq, key=lambda b: _total_order_key(b, w))
+
+
+@pytest.mark.parametrize("fdt", [np.float32, np.float64])
+def test_float_finite_matches_numpy_sort(fdt):
+    rng = np.random.default_rng(9)
+    vals = rng.standard_normal(300).astype(fdt) * 1e3
+    x = vals[rng.integers(0, vals.size, size=20_000)]
+    x[x == 0] = 1
+    assert np.array_equal(O.frequency_sort_any(x), np.sort(x))
+    pi = O.stable_argsort_any(x)
+    assert np.array_equal(pi, np.argsort(x, kind="stable").astype(np.uint32))
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64, np.float32, np.float64])
+def test_ordered_signed_round_trip(dtype):
+    rng = np.random.default_rng(11)
+    w = np.dtype(dtype).itemsize
+    raw = rng.integers(0, 256, size=4096 * w, dtype=np.uint8).view(dtype)
+    back = O.from_ordered_signed(O.ordered_signed(raw), dtype)
+    assert np.array_equal(back.view(np.uint8), raw.view(np.uint8))
+
+
 def test_is_monotone_brute_force():
     for length in range(0, 6):
         for seq in itertools.product([0, 1, 2], repeat=length):
