@@ -50,7 +50,25 @@
 extern "C" {
 #endif
 
-typedef enum { CAFS_INT32 = 0, CAFS_INT64 = 1 } cafs_dtype;
+/* Key types.  Signed integers sort in their natural order (the paper ships
+ * int32/int64, Sec. 5).  Unsigned integers sort in their natural order and
+ * IEEE-754 floats in the standard's totalOrder (negative NaNs, -inf, negative
+ * numbers, -0, +0, positive numbers, +inf, positive NaNs; equal keys are
+ * equal bit patterns): the library maps them onto signed integers of the same
+ * width by an order-preserving bijection (unsigned: flip the sign bit; float:
+ * flip the magnitude bits of negative values), sorts those, and maps the
+ * output back, one extra elementwise read and write of the column each way.
+ * cafs_sort, cafs_sort_ex, cafs_sort_host, cafs_estimate_k and cafs_argsort
+ * accept every type; the batched, served and allocation-free entry points
+ * take CAFS_INT32 and CAFS_INT64 only (else CAFS_ERR_UNSUPPORTED_DTYPE). */
+typedef enum {
+  CAFS_INT32 = 0,
+  CAFS_INT64 = 1,
+  CAFS_UINT32 = 2,
+  CAFS_UINT64 = 3,
+  CAFS_FLOAT32 = 4,
+  CAFS_FLOAT64 = 5
+} cafs_dtype;
 
 typedef enum {
   CAFS_OK = 0,

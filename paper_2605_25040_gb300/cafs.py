@@ -16,7 +16,9 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcafs.so")
 
-INT32, INT64 = 0, 1
+INT32, INT64, UINT32, UINT64, FLOAT32, FLOAT64 = 0, 1, 2, 3, 4, 5
+KEY_TYPES = {"int32": (INT32, 4), "int64": (INT64, 8), "uint32": (UINT32, 4), "uint64": (UINT64, 8),
+             "float32": (FLOAT32, 4), "float64": (FLOAT64, 8)}
 
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "unsupported dtype", 3: "too large", 4: "alias",
@@ -178,11 +180,29 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 
 def _dtype_code(dtype) -> int:
     import torch
-    if dtype in (torch.int64, np.int64, np.dtype(np.int64)):
-        return INT64
-    if dtype in (torch.int32, np.int32, np.dtype(np.int32)):
-        return INT32
-    raise TypeError(f"unsupported key dtype {dtype}: int32 or int64 only")
+    names = {torch.int64: "int64", torch.int32: "int32", torch.float32: "float32", torch.float64: "float64"}
+    for attr in ("uint32", "uint64"):
+        if hasattr(torch, attr):
+            names[getattr(torch, attr)] = attr
+    if isinstance(dtype, torch.dtype):
+        if dtype in names:
+            return KEY_TYPES[names[dtype]][0]
+    else:
+        name = np.dtype(dtype).name
+        if name in KEY_TYPES:
+            return KEY_TYPES[name][0]
+    raise TypeError(f"unsupported key dtype {dtype}")
+
+
+def _key_code(t, key_type) -> int:
+    """The key type of tensor t, or ``key_type`` (a name of KEY_TYPES) read
+    from t's bits when given (e.g. uint64 keys held in an int64 tensor)."""
+    if key_type is None:
+        return _dtype_code(t.dtype)
+    code, width = KEY_TYPES[str(key_type)]
+    if t.element_size() != width:
+        raise ValueError(f"key_type {key_type} needs {width}-byte elements")
+    return code
 
 
 def _check(code: int, what: str) -> None:
@@ -206,8 +226,10 @@ def _device_tensor(t):
     return t
 
 
-def sort(keys, out=None, stream=None):
-    """Sorts a 1-D int32/int64 CUDA tensor ascending; returns ``out``."""
+def sort(keys, out=None, stream=None, key_type=None):
+    """Sorts a 1-D CUDA tensor of keys ascending (int32/int64/uint32/uint64/
+    float32/float64; ``key_type`` names the type when the tensor's dtype only
+    holds the bits); returns ``out``."""
     import torch
     lib = load()
     keys = _device_tensor(keys)
@@ -216,12 +238,12 @@ def sort(keys, out=None, stream=None):
     if out.dtype != keys.dtype or out.numel() != keys.numel() or not out.is_contiguous():
         raise ValueError("out must match keys in dtype and size")
     with torch.cuda.device(keys.device):
-        _check(lib.cafs_sort(keys.data_ptr(), keys.numel(), _dtype_code(keys.dtype), out.data_ptr(),
+        _check(lib.cafs_sort(keys.data_ptr(), keys.numel(), _key_code(keys, key_type), out.data_ptr(),
                              _stream_handle(stream)), "cafs_sort")
     return out
 
 
-def sort_ex(keys, out=None, stream=None):
+def sort_ex(keys, out=None, stream=None, key_type=None):
     """Like ``sort`` but waits and returns (out, report dict)."""
     import torch
     lib = load()
@@ -230,13 +252,13 @@ def sort_ex(keys, out=None, stream=None):
         out = torch.empty_like(keys)
     rep = Report()
     with torch.cuda.device(keys.device):
-        _check(lib.cafs_sort_ex(keys.data_ptr(), keys.numel(), _dtype_code(keys.dtype),
+        _check(lib.cafs_sort_ex(keys.data_ptr(), keys.numel(), _key_code(keys, key_type),
                                 out.data_ptr(), ctypes.byref(rep), _stream_handle(stream)),
                "cafs_sort_ex")
     return out, rep.as_dict()
 
 
-def argsort(keys, out=None, perm=None, stream=None, report: bool = False):
+def argsort(keys, out=None, perm=None, stream=None, report: bool = False, key_type=None):
     """Stable argsort of a 1-D int32/int64 CUDA tensor: returns (sorted keys,
     perm) with keys[perm] == sorted keys and equal keys in input order
     (perm is int32 holding the uint32 positions); with ``report`` also the
@@ -254,7 +276,7 @@ def argsort(keys, out=None, perm=None, stream=None, report: bool = False):
         raise ValueError("perm must be a contiguous int32 tensor of keys' size")
     rep = Report() if report else None
     with torch.cuda.device(keys.device):
-        _check(lib.cafs_argsort(keys.data_ptr(), keys.numel(), _dtype_code(keys.dtype), out.data_ptr(),
+        _check(lib.cafs_argsort(keys.data_ptr(), keys.numel(), _key_code(keys, key_type), out.data_ptr(),
                                 perm.data_ptr(), ctypes.byref(rep) if report else None,
                                 _stream_handle(stream)), "cafs_argsort")
     if report:
@@ -268,14 +290,14 @@ def set_hash_seed(seed: int) -> None:
     load().cafs_set_hash_seed(int(seed) & 0xFFFFFFFFFFFFFFFF)
 
 
-def estimate_k(keys, stream=None) -> dict:
+def estimate_k(keys, stream=None, key_type=None) -> dict:
     """Sampler + Chao1 + dispatcher result for a CUDA tensor of keys."""
     import torch
     lib = load()
     keys = _device_tensor(keys)
     est = Estimate()
     with torch.cuda.device(keys.device):
-        _check(lib.cafs_estimate_k(keys.data_ptr(), keys.numel(), _dtype_code(keys.dtype),
+        _check(lib.cafs_estimate_k(keys.data_ptr(), keys.numel(), _key_code(keys, key_type),
                                    ctypes.byref(est), _stream_handle(stream)), "cafs_estimate_k")
     return est.as_dict()
 

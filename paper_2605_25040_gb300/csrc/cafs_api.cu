@@ -12,6 +12,7 @@
 #include "cafs.h"
 #include "cafs_argsort.h"
 #include "cafs_internal.h"
+#include "cafs_transform.h"
 
 namespace cafs {
 namespace {
@@ -194,11 +195,23 @@ Workspace* workspace_for(int dev, cudaStream_t s) {
   return w;
 }
 
-cafs_status check_args_impl(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out) {
-  if (dtype != CAFS_INT32 && dtype != CAFS_INT64) return CAFS_ERR_UNSUPPORTED_DTYPE;
+// Key types: element width, the signed type the pipeline sorts (0: int32,
+// 1: int64) and the order map onto it (0: none, 1: unsigned, 2: IEEE float).
+bool known_type(cafs_dtype t) { return t >= CAFS_INT32 && t <= CAFS_FLOAT64; }
+size_t type_width(cafs_dtype t) { return (t == CAFS_INT64 || t == CAFS_UINT64 || t == CAFS_FLOAT64) ? 8 : 4; }
+int base_type(cafs_dtype t) { return type_width(t) == 8 ? 1 : 0; }
+int order_kind(cafs_dtype t) {
+  return (t == CAFS_UINT32 || t == CAFS_UINT64) ? 1 : (t == CAFS_FLOAT32 || t == CAFS_FLOAT64) ? 2 : 0;
+}
+
+// `any_type`: the entry point takes every key type (else int32/int64 only).
+cafs_status check_args_impl(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out,
+                            bool any_type = false) {
+  if (any_type ? !known_type(dtype) : (dtype != CAFS_INT32 && dtype != CAFS_INT64))
+    return CAFS_ERR_UNSUPPORTED_DTYPE;
   if (n == 0) return CAFS_OK;
   if ((unsigned long long)n > 0xFFFFFFFFull) return CAFS_ERR_TOO_LARGE;
-  const size_t kb = dtype == CAFS_INT64 ? 8 : 4;
+  const size_t kb = type_width(dtype);
   if (!keys || (need_out && !out)) return CAFS_ERR_INVALID_ARGUMENT;
   if (reinterpret_cast<uintptr_t>(keys) % kb) return CAFS_ERR_INVALID_ARGUMENT;
   if (need_out) {
@@ -299,9 +312,16 @@ void fill_report_impl(const Record& r, cafs_report* rep) {
   for (int i = 0; i < 6; ++i) rep->timeline_ns[i] = r.timeline[i];
 }
 
+// The order map of key type t applied to n keys src -> dst (counted launch).
+cafs_status map_keys(const void* src, void* dst, unsigned long long n, cafs_dtype t, cudaStream_t s) {
+  if (launch_order_map(src, dst, n, (int)type_width(t), order_kind(t), s) != cudaSuccess) return CAFS_ERR_CUDA;
+  g_launches++;
+  return CAFS_OK;
+}
+
 cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, cafs_report* report,
                       void* stream) {
-  cafs_status st = check_args_impl(keys, n, dtype, out, true);
+  cafs_status st = check_args_impl(keys, n, dtype, out, true, true);
   if (st != CAFS_OK) return st;
   if (n == 0) {
     if (report) {
@@ -318,8 +338,16 @@ cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, c
   DeviceInfo* d = nullptr;
   if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
   Workspace* w = workspace_for(dev, s);
-  if ((st = ensure_workspace(w, n, dtype, s, false)) != CAFS_OK) return st;
-  if ((st = enqueue(w, d, keys, out, n, dtype, kModeSort, s)) != CAFS_OK) return st;
+  const int bt = base_type(dtype);
+  if ((st = ensure_workspace(w, n, bt, s, false)) != CAFS_OK) return st;
+  if (order_kind(dtype)) {
+    // keys -> out in the signed order, sorted in place, mapped back
+    if ((st = map_keys(keys, out, n, dtype, s)) != CAFS_OK) return st;
+    if ((st = enqueue(w, d, out, out, n, bt, kModeSort, s)) != CAFS_OK) return st;
+    if ((st = map_keys(out, out, n, dtype, s)) != CAFS_OK) return st;
+  } else if ((st = enqueue(w, d, keys, out, n, bt, kModeSort, s)) != CAFS_OK) {
+    return st;
+  }
   if (report) {
     Record r;
     if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
@@ -331,7 +359,7 @@ cafs_status sort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, c
 // Stable argsort of one column (keys, out and perm pairwise disjoint).
 cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out, uint32_t* perm,
                          cafs_report* report, void* stream) {
-  cafs_status st = check_args_impl(keys, n, dtype, out, true);
+  cafs_status st = check_args_impl(keys, n, dtype, out, true, true);
   if (st != CAFS_OK) return st;
   if (n == 0) {
     if (report) {
@@ -342,7 +370,7 @@ cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out
     return CAFS_OK;
   }
   if (!perm || reinterpret_cast<uintptr_t>(perm) % 4) return CAFS_ERR_INVALID_ARGUMENT;
-  const uintptr_t kb = dtype == CAFS_INT64 ? 8 : 4;
+  const uintptr_t kb = type_width(dtype);
   const uintptr_t k0 = reinterpret_cast<uintptr_t>(keys), o0 = reinterpret_cast<uintptr_t>(out);
   const uintptr_t p0 = reinterpret_cast<uintptr_t>(perm);
   const uintptr_t kbytes = (uintptr_t)n * kb, pbytes = (uintptr_t)n * 4;
@@ -356,7 +384,9 @@ cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out
   DeviceInfo* d = nullptr;
   if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
   Workspace* w = workspace_for(dev, s);
-  if ((st = ensure_workspace(w, n, dtype, s, false)) != CAFS_OK) return st;
+  const int bt = base_type(dtype);
+  const bool mapped = order_kind(dtype) != 0;
+  if ((st = ensure_workspace(w, n, bt, s, mapped)) != CAFS_OK) return st;
   if ((unsigned long long)n > w->arg_n) {
     if (w->arg) {
       if (cudaStreamSynchronize(s) != cudaSuccess) return CAFS_ERR_CUDA;
@@ -369,19 +399,27 @@ cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out
     }
     w->arg_n = n;
   }
+  // other key types: their signed images in the io buffer (the kernel reads
+  // the keys again after the sorted keys are written)
+  const void* src = keys;
+  if (mapped) {
+    if ((st = map_keys(keys, w->io, n, dtype, s)) != CAFS_OK) return st;
+    src = w->io;
+  }
   if (cudaMemsetAsync(w->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
   ArgsortParams ap;
-  ap.p = pipeline_params(w, keys, out, n, kModeSort);
+  ap.p = pipeline_params(w, src, out, n, kModeSort);
   ap.perm = perm;
   ap.rk = w->arg;
   ap.iv = w->arg + n;
   ap.tv = w->arg + 2 * (size_t)n;
   ap.rk2 = w->arg + 3 * (size_t)n;
   cudaError_t e;
-  if (n < kSmallN) e = launch_small_argsort(ap, dtype, s);
-  else e = launch_argsort(ap, dtype, launch_grid(n, d->max_grid_arg[dtype]), s);
+  if (n < kSmallN) e = launch_small_argsort(ap, bt, s);
+  else e = launch_argsort(ap, bt, launch_grid(n, d->max_grid_arg[bt]), s);
   if (e != cudaSuccess) return CAFS_ERR_CUDA;
   g_launches++;
+  if (mapped && (st = map_keys(out, out, n, dtype, s)) != CAFS_OK) return st;
   if (report) {
     Record r;
     if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
@@ -429,7 +467,7 @@ cafs_status cafs_argsort(const void* keys, size_t n, cafs_dtype dtype, void* out
 cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype, cafs_estimate* est,
                             void* stream) {
   if (!est) return CAFS_ERR_INVALID_ARGUMENT;
-  cafs_status st = check_args_impl(keys, n, dtype, nullptr, false);
+  cafs_status st = check_args_impl(keys, n, dtype, nullptr, false, true);
   if (st != CAFS_OK) return st;
   std::memset(est, 0, sizeof(*est));
   if (n == 0) {
@@ -443,8 +481,15 @@ cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype, cafs_e
   DeviceInfo* d = nullptr;
   if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
   Workspace* w = workspace_for(dev, s);
-  if ((st = ensure_workspace(w, n, dtype, s, false)) != CAFS_OK) return st;
-  if ((st = enqueue(w, d, keys, nullptr, n, dtype, kModeEstimate, s)) != CAFS_OK) return st;
+  const int bt = base_type(dtype);
+  const bool mapped = order_kind(dtype) != 0;
+  if ((st = ensure_workspace(w, n, bt, s, mapped)) != CAFS_OK) return st;
+  const void* src = keys;
+  if (mapped) {
+    if ((st = map_keys(keys, w->io, n, dtype, s)) != CAFS_OK) return st;
+    src = w->io;
+  }
+  if ((st = enqueue(w, d, src, nullptr, n, bt, kModeEstimate, s)) != CAFS_OK) return st;
   Record r;
   if ((st = read_record(w, s, &r)) != CAFS_OK) return st;
   if (r.status != kDevOk) return (cafs_status)r.status;
@@ -454,7 +499,7 @@ cafs_status cafs_estimate_k(const void* keys, size_t n, cafs_dtype dtype, cafs_e
 
 cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype, void* host_out,
                            cafs_report* report, void* stream) {
-  cafs_status st = check_args_impl(host_keys, n, dtype, host_out, false);
+  cafs_status st = check_args_impl(host_keys, n, dtype, host_out, false, true);
   if (st != CAFS_OK) return st;
   if (n && !host_out) return CAFS_ERR_INVALID_ARGUMENT;
   if (n == 0) {
@@ -464,7 +509,7 @@ cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype, vo
     }
     return CAFS_OK;
   }
-  const size_t bytes = n * (dtype == CAFS_INT64 ? 8 : 4);
+  const size_t bytes = n * type_width(dtype);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;
@@ -472,9 +517,12 @@ cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype, vo
   DeviceInfo* d = nullptr;
   if ((st = ensure_device(dev, &d)) != CAFS_OK) return st;
   Workspace* w = workspace_for(dev, s);
-  if ((st = ensure_workspace(w, n, dtype, s, true)) != CAFS_OK) return st;
+  const int bt = base_type(dtype);
+  if ((st = ensure_workspace(w, n, bt, s, true)) != CAFS_OK) return st;
   if (cudaMemcpyAsync(w->io, host_keys, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return CAFS_ERR_CUDA;
-  if ((st = enqueue(w, d, w->io, w->io, n, dtype, kModeSort, s)) != CAFS_OK) return st;
+  if (order_kind(dtype) && (st = map_keys(w->io, w->io, n, dtype, s)) != CAFS_OK) return st;
+  if ((st = enqueue(w, d, w->io, w->io, n, bt, kModeSort, s)) != CAFS_OK) return st;
+  if (order_kind(dtype) && (st = map_keys(w->io, w->io, n, dtype, s)) != CAFS_OK) return st;
   if (cudaMemcpyAsync(host_out, w->io, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CAFS_ERR_CUDA;
   Record r;
   if ((st = read_record(w, s, &r)) != CAFS_OK) return st;

@@ -79,6 +79,22 @@ def test_argsort_argument_errors_are_synchronous(lib):
     assert lib.cafs_argsort(p, 4, cafs.INT32, p + 64, p + 72, None, None) == 4
 
 
+def test_key_types(lib):
+    buf = (ctypes.c_int64 * 64)()
+    p = ctypes.addressof(buf)
+    # 8-byte key types need 8-byte alignment, 4-byte ones 4-byte
+    assert lib.cafs_sort(p + 4, 4, cafs.UINT64, p + 64, None) == 1
+    assert lib.cafs_sort(p + 4, 4, cafs.FLOAT64, p + 64, None) == 1
+    assert lib.cafs_sort(p, 8, cafs.FLOAT32, p + 4, None) == 4
+    # the allocation-free, batched and served entry points take int32/int64 only
+    for t in (cafs.UINT32, cafs.UINT64, cafs.FLOAT32, cafs.FLOAT64):
+        assert lib.cafs_sort_noalloc(p, 4, t, p + 64, None) == 2
+        cols = (cafs.Column * 1)()
+        cols[0].keys, cols[0].out, cols[0].n, cols[0].dtype = p, p + 256, 8, t
+        assert lib.cafs_sort_batch(cols, 1, None, None) == 2
+    assert cafs.KEY_TYPES["float64"] == (cafs.FLOAT64, 8)
+
+
 def test_names(lib):
     assert lib.cafs_status_string(0) == b"ok"
     assert lib.cafs_path_string(4) == b"main"
