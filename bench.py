@@ -21,7 +21,8 @@ cpu_baseline = the CPU oracle on a bounded sample of the same columns.
 
 Three more legs (rank 0; --no-argsort / --no-batched / --no-served skip them):
   argsort: cafs_argsort (sorted keys plus the stable permutation) on four
-    sweep columns, checked against and timed beside torch.sort(stable=True);
+    sweep columns, checked against and timed beside torch.sort(stable=True),
+    and two sweep columns' bits sorted as uint64 and float64 keys;
   batched: 4096 int64 columns (N log-uniform [1e3, 1e6], K log-uniform
     [2, min(N/4, 5e4)], Zipf 1.1) and 64 mixed int32/int64 columns (N 1e3..3e7,
     K 2..N, 4 spill-trigger columns): one recorded batched launch (default
@@ -279,6 +280,35 @@ def bench_argsort(torch, cafs, dev_in, names, peak, want=("uniform_K4", "uniform
     return res
 
 
+def bench_key_types(torch, cafs, dev_in, names, col_ms, want=("uniform_K200", "uniform_K30000000")):
+    """The same sweep columns' bits sorted as uint64 and as float64 keys
+    (order-preserving map, signed sort, map back), checked against torch's
+    signed sort of the mapped bits and timed beside the int64 sort."""
+    res = {"timing": "CUDA events on the current stream, median of 5 after 2 warm-ups; inputs larger than L2",
+           "columns": []}
+    ok_all = True
+    sign = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    for i, (name, x) in enumerate(zip(names, dev_in)):
+        if name not in want:
+            continue
+        out = torch.empty_like(x)
+        row = {"column": name, "int64_ms": round(col_ms[i], 4)}
+        for kt in ("uint64", "float64"):
+            ms, _ = _time_ms(torch, lambda: cafs.sort(x, out, key_type=kt))
+            mapped = x ^ sign if kt == "uint64" else torch.where(x < 0, x ^ ~sign, x)
+            ref = torch.sort(mapped).values
+            ref = ref ^ sign if kt == "uint64" else torch.where(ref < 0, ref ^ ~sign, ref)
+            ok_all &= bool(torch.equal(ref, out))
+            del mapped, ref
+            row[kt + "_ms"] = round(ms, 4)
+            row[kt + "_gkeys_s"] = round(x.numel() / (ms / 1e3) / 1e9, 2)
+        res["columns"].append(row)
+        del out
+    res["verified_vs_torch_sort_of_mapped_bits"] = ok_all
+    torch.cuda.empty_cache()
+    return res
+
+
 def bench_batched(torch, cafs):
     from paper_2605_25040_gb300 import datagen as G
     res = {}
@@ -397,7 +427,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-form measurement")
-    ap.add_argument("--no-argsort", action="store_true", help="skip the argsort measurement")
+    ap.add_argument("--no-argsort", action="store_true", help="skip the argsort and key-type measurements")
     ap.add_argument("--columns", default="",
                     help="comma-separated subset of sweep columns (e.g. uniform_K200); default all")
     args = ap.parse_args()
@@ -545,9 +575,10 @@ def main():
                "blocking_per_column": {"value": n * ncol * e2e_steps * world / dt_blocking / 1e9,
                                        "api": "cafs_sort_host, one column at a time"}}
 
-    argsort = None
+    argsort = key_types = None
     if rank == 0 and not args.no_argsort:
         argsort = bench_argsort(torch, cafs, dev_in, names, peak)
+        key_types = bench_key_types(torch, cafs, dev_in, names, col_ms)
 
     batched = served = None
     if rank == 0 and not args.no_batched:
@@ -598,6 +629,7 @@ def main():
         "batched": batched,
         "served": served,
         "argsort": argsort,
+        "key_types": key_types,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
