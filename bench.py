@@ -22,7 +22,8 @@ cpu_baseline = the CPU oracle on a bounded sample of the same columns.
 Three more legs (rank 0; --no-argsort / --no-batched / --no-served skip them):
   argsort: cafs_argsort (sorted keys plus the stable permutation) on four
     sweep columns, checked against and timed beside torch.sort(stable=True),
-    and two sweep columns' bits sorted as uint64 and float64 keys;
+    two sweep columns' bits sorted as uint64 and float64 keys, and five
+    input profiles (runs of equal keys, one group per key, nearly sorted);
   batched: 4096 int64 columns (N log-uniform [1e3, 1e6], K log-uniform
     [2, min(N/4, 5e4)], Zipf 1.1) and 64 mixed int32/int64 columns (N 1e3..3e7,
     K 2..N, 4 spill-trigger columns): one recorded batched launch (default
@@ -309,6 +310,33 @@ def bench_key_types(torch, cafs, dev_in, names, col_ms, want=("uniform_K200", "u
     return res
 
 
+def bench_profiles(torch, cafs, n, peak):
+    """Input profiles at N = 3e7 int64: runs of equal keys, one group per key,
+    a nearly sorted column; checked against torch.sort."""
+    from paper_2605_25040_gb300 import datagen as G
+    cases = [("runs_mean64_zipf_K4096", lambda: G.runs_column(n, 4096, 64.0, "zipf", np.int64, seed=1)),
+             ("runs_mean4_K200", lambda: G.runs_column(n, 200, 4.0, "uniform", np.int64, seed=2)),
+             ("grouped_K200", lambda: G.grouped_column(n, 200, np.int64, seed=3)),
+             ("grouped_K100000", lambda: G.grouped_column(n, 100_000, np.int64, seed=4)),
+             ("almost_sorted_K200_swaps3000", lambda: G.almost_sorted(n, 200, 3000, np.int64, seed=5))]
+    res = {"timing": "CUDA events on the current stream, median of 5 after 2 warm-ups; inputs larger than L2",
+           "columns": []}
+    ok_all = True
+    for name, make in cases:
+        x = torch.from_numpy(make()).cuda()
+        out = torch.empty_like(x)
+        ms, _ = _time_ms(torch, lambda: cafs.sort(x, out))
+        _, rep = cafs.sort_ex(x, out)
+        ok_all &= bool(torch.equal(torch.sort(x).values, out))
+        res["columns"].append({"column": name, "path": cafs.path_name(rep["path"]), "ms": round(ms, 4),
+                               "gkeys_s": round(n / (ms / 1e3) / 1e9, 2),
+                               "frac_hbm": round(16 * n / (ms / 1e3) / 1e9 / peak, 4)})
+        del x, out
+    res["verified_vs_torch_sort"] = ok_all
+    torch.cuda.empty_cache()
+    return res
+
+
 def bench_batched(torch, cafs):
     from paper_2605_25040_gb300 import datagen as G
     res = {}
@@ -427,7 +455,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-form measurement")
-    ap.add_argument("--no-argsort", action="store_true", help="skip the argsort and key-type measurements")
+    ap.add_argument("--no-argsort", action="store_true",
+                    help="skip the argsort, key-type and input-profile measurements")
     ap.add_argument("--columns", default="",
                     help="comma-separated subset of sweep columns (e.g. uniform_K200); default all")
     args = ap.parse_args()
@@ -575,10 +604,12 @@ def main():
                "blocking_per_column": {"value": n * ncol * e2e_steps * world / dt_blocking / 1e9,
                                        "api": "cafs_sort_host, one column at a time"}}
 
-    argsort = key_types = None
+    argsort = key_types = profiles = None
     if rank == 0 and not args.no_argsort:
         argsort = bench_argsort(torch, cafs, dev_in, names, peak)
         key_types = bench_key_types(torch, cafs, dev_in, names, col_ms)
+        if n == 30_000_000:
+            profiles = bench_profiles(torch, cafs, n, peak)
 
     batched = served = None
     if rank == 0 and not args.no_batched:
@@ -630,6 +661,7 @@ def main():
         "served": served,
         "argsort": argsort,
         "key_types": key_types,
+        "profiles": profiles,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -173,6 +173,59 @@ def sorted_column(n: int, k: int, dtype=np.int64, seed: int = 0) -> np.ndarray:
     return np.sort(column(n, k, "uniform", dtype, seed))
 
 
+# Input profiles (SURVEY's input-profile row): runs of equal keys, one
+# contiguous group per key, and a nearly sorted column.
+
+def _group_sizes(n: int, k: int, seed: int) -> np.ndarray:
+    """K positive sizes summing to N (uniform random proportions)."""
+    w = _unit_float(splitmix64(seed, k)) + 1e-3
+    sizes = np.floor(w / w.sum() * (n - k)).astype(np.int64) + 1
+    sizes[0] += n - int(sizes.sum())
+    return sizes
+
+
+def runs_column(n: int, k: int, mean_run: float, dist: str = "uniform", dtype=np.int64,
+                seed: int = 0, s: float = 1.1) -> np.ndarray:
+    """Runs of equal keys: geometric run lengths with mean ``mean_run`` (>= 1),
+    each run's value drawn (uniform or Zipf) from a palette of K values; a key
+    recurs in many runs."""
+    base = 77 + n + k
+    p = 1.0 / max(mean_run, 1.0)
+    m = int(n / mean_run * 1.5) + 16
+    u = _unit_float(splitmix64(base ^ seed, m))
+    lengths = np.ones(m, dtype=np.int64) if p >= 1.0 else \
+        1 + np.floor(np.log1p(-u) / np.log1p(-p)).astype(np.int64)
+    ends = np.cumsum(lengths)
+    runs = int(np.searchsorted(ends, n)) + 1
+    lengths = lengths[:runs]
+    lengths[-1] -= int(ends[runs - 1]) - n
+    pal = distinct_values(k, base ^ seed, dtype)
+    ranks = (zipf_ranks(runs, k, s, base * 31 + seed) if dist == "zipf"
+             else uniform_ranks(runs, k, base * 31 + seed))
+    return np.repeat(pal[ranks], lengths).astype(dtype, copy=False)
+
+
+def grouped_column(n: int, k: int, dtype=np.int64, seed: int = 0) -> np.ndarray:
+    """Every one of K values in exactly one contiguous group, groups in random
+    order (a column already grouped by key, e.g. the output of a group-by)."""
+    base = 91 + n + k
+    pal = shuffle(distinct_values(k, base ^ seed, dtype), base + seed)
+    return np.repeat(pal, _group_sizes(n, k, base * 7 + seed)).astype(dtype, copy=False)
+
+
+def almost_sorted(n: int, k: int, swaps: int, dtype=np.int64, seed: int = 0) -> np.ndarray:
+    """A non-decreasing column over K values with ``swaps`` random pairs of
+    positions exchanged."""
+    base = 113 + n + k
+    pal = np.sort(distinct_values(k, base ^ seed, dtype))
+    out = np.repeat(pal, _group_sizes(n, k, base * 7 + seed)).astype(dtype, copy=False)
+    if swaps and n > 1:
+        ij = _uniform_index(splitmix64(base * 13 + seed, 2 * swaps), n).reshape(swaps, 2)
+        for i, j in ij:
+            out[i], out[j] = out[j], out[i]
+    return out
+
+
 def log_uniform_int(lo: float, hi: float, count: int, seed: int) -> np.ndarray:
     """Integers log-uniform in [lo, hi]."""
     u = _unit_float(splitmix64(seed, count))

@@ -46,3 +46,18 @@ def test_specs_follow_the_recipes():
     assert sum(1 for m in mixed if m[3] == "spill") == 4
     assert sum(1 for m in mixed if m[0] == m[1]) >= 10           # K = N columns
     assert {m[2] for m in mixed} == {"int32", "int64"}
+
+
+def test_input_profiles_have_their_shape():
+    x = G.runs_column(100_000, 300, 16.0, "zipf", np.int64, seed=3)
+    assert x.size == 100_000 and np.array_equal(x, G.runs_column(100_000, 300, 16.0, "zipf", np.int64, seed=3))
+    runs = 1 + int(np.count_nonzero(x[1:] != x[:-1]))
+    assert 100_000 / 16.0 * 0.8 < runs < 100_000 / 16.0 * 1.2   # geometric runs, mean ~16
+    g = G.grouped_column(50_000, 700, np.int32, seed=4)
+    assert g.size == 50_000 and g.dtype == np.int32
+    starts = np.flatnonzero(np.r_[True, g[1:] != g[:-1]])
+    assert starts.size == 700 and np.unique(g).size == 700        # one contiguous group per key
+    a = G.almost_sorted(50_000, 500, 40, np.int64, seed=5)
+    assert np.count_nonzero(a[1:] < a[:-1]) <= 2 * 40
+    assert np.count_nonzero(G.almost_sorted(50_000, 500, 0, np.int64, seed=5)[1:] <
+                            G.almost_sorted(50_000, 500, 0, np.int64, seed=5)[:-1]) == 0

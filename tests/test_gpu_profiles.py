@@ -1,0 +1,54 @@
+"""Input profiles (runs of equal keys, one group per key, nearly sorted):
+sorted keys, branch and argsort permutation equal the oracle's."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cafs_oracle as O  # noqa: E402
+from paper_2605_25040_gb300 import cafs  # noqa: E402
+from paper_2605_25040_gb300 import datagen as G  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_25040_gb300 import build
+    build.build()
+    cafs.load()
+    yield
+
+
+def check(x, argsort=False):
+    xt = torch.from_numpy(x).cuda()
+    out, rep = cafs.sort_ex(xt)
+    assert rep["device_status"] == 0
+    assert np.array_equal(out.cpu().numpy(), O.frequency_sort(x))
+    assert rep["path"] == O.final_path(x), (O.PATH_NAMES[rep["path"]], O.PATH_NAMES[O.final_path(x)])
+    if argsort:
+        _, perm = cafs.argsort(xt)
+        assert np.array_equal(perm.cpu().numpy().view(np.uint32), O.stable_argsort(x))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("k,mean_run,dist", [(4, 1000.0, "uniform"), (200, 8.0, "uniform"),
+                                             (4096, 64.0, "zipf"), (50_000, 3.0, "zipf")])
+def test_runs(dtype, k, mean_run, dist):
+    check(G.runs_column(300_000, k, mean_run, dist, dtype, seed=k), argsort=(k == 200))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("k", [1, 8, 200, 4096, 100_000])
+def test_grouped(dtype, k):
+    check(G.grouped_column(300_000, k, dtype, seed=k), argsort=(k == 4096))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("k,swaps", [(8, 1), (200, 30), (4096, 300), (300_000, 1000)])
+def test_almost_sorted(dtype, k, swaps):
+    check(G.almost_sorted(300_000, k, swaps, dtype, seed=k), argsort=(k == 200))
+    check(G.almost_sorted(300_000, k, 0, dtype, seed=k))   # sorted: the bypass
