@@ -134,6 +134,7 @@ struct cafs_server {
   // statistics
   uint64_t launches = 0, completed = 0, keys_done = 0;
   size_t peak_arena_used = 0, arena_used = 0;
+  unsigned dispatching = 0;   // a launch is being enqueued (scheduler or submitter): one at a time
 };
 
 namespace cafs {
@@ -217,7 +218,8 @@ void scheduler_loop(cafs_server* sv) {
       std::unique_lock<std::mutex> lk(sv->mu);
       for (;;) {
         if (sv->stop) return;
-        if (!sv->pending.empty() && !sv->free_launches.empty()) {
+        // one thread enqueues at a time (the launches share streams and events)
+        if (!sv->pending.empty() && !sv->free_launches.empty() && sv->dispatching == 0) {
           // Admission by memory budget, first come first served.
           while (!sv->pending.empty() && batch.size() < sv->max_batch) {
             Request* r = sv->pending.front();
@@ -233,6 +235,7 @@ void scheduler_loop(cafs_server* sv) {
             L = sv->free_launches.back();
             sv->free_launches.pop_back();
             idle = sv->inflight.empty();
+            sv->dispatching++;
             break;
           }
         }
@@ -248,6 +251,7 @@ void scheduler_loop(cafs_server* sv) {
         if (st != CAFS_OK && sv->fatal == CAFS_OK) sv->fatal = st;
         sv->inflight.push_back(L);
         sv->launches++;
+        sv->dispatching--;
       }
       sv->cv_done.notify_one();
       continue;
@@ -290,6 +294,7 @@ void scheduler_loop(cafs_server* sv) {
       if (st != CAFS_OK && sv->fatal == CAFS_OK) sv->fatal = st;
       sv->inflight.push_back(L);
       sv->launches++;
+      sv->dispatching--;
     }
     sv->cv_done.notify_one();
   }
@@ -468,6 +473,7 @@ cafs_status submit_at(cafs_server* sv, const void* host_keys, size_t n, cafs_dty
   if ((unsigned long long)n > sv->max_request_keys) return CAFS_ERR_TOO_LARGE;
   const unsigned long long bytes = (unsigned long long)n * (dtype == CAFS_INT64 ? 8 : 4);
   if (((bytes + kArenaAlign - 1) & ~(kArenaAlign - 1)) > sv->arena.size()) return CAFS_ERR_TOO_LARGE;
+  Launch* direct = nullptr;
   Request* r = new Request();
   r->host_in = host_keys;
   r->host_out = host_out;
@@ -487,10 +493,43 @@ cafs_status submit_at(cafs_server* sv, const void* host_keys, size_t n, cafs_dty
       r->report.path = CAFS_PATH_EMPTY;
       r->t_done = r->t_arrival;
       r->done = true;
+    } else if (sv->pending.empty() && sv->inflight.empty() && sv->dispatching == 0 &&
+               !sv->free_launches.empty()) {
+      // An idle server: this thread launches the request itself (the
+      // scheduler's wake-up would only add latency).
+      const unsigned long long off = sv->arena.alloc(r->bytes);
+      if (off != ~0ull) {
+        r->off = off;
+        sv->arena_used += (r->bytes + kArenaAlign - 1) & ~(kArenaAlign - 1);
+        sv->peak_arena_used = std::max(sv->peak_arena_used, sv->arena_used);
+        direct = sv->free_launches.back();
+        sv->free_launches.pop_back();
+        sv->dispatching++;
+      } else {
+        sv->pending.push_back(r);
+      }
     } else {
       sv->pending.push_back(r);
     }
     *ticket = r->ticket;
+  }
+  if (direct) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != sv->device) cudaSetDevice(sv->device);
+    const cafs_status est = enqueue_solo(sv, r, direct);
+    if (prev >= 0 && prev != sv->device) cudaSetDevice(prev);
+    direct->reqs.assign(1, r);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (est != CAFS_OK && sv->fatal == CAFS_OK) sv->fatal = est;
+      sv->inflight.push_back(direct);
+      sv->launches++;
+      sv->dispatching--;
+    }
+    sv->cv_done.notify_one();
+    sv->cv_sched.notify_one();   // requests that queued meanwhile
+    return CAFS_OK;
   }
   if (n) sv->cv_sched.notify_one();
   else sv->cv_client.notify_all();
