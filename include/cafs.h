@@ -343,7 +343,7 @@ cafs_status cafs_serial_run_trace(const cafs_request* reqs, size_t nreq, const d
                                   double* latency_us, cafs_report* reports, double* elapsed_s,
                                   void* stream);
 
-/* Hash seed (SURVEY's randomised-seed row; Eq. 4 fixes the golden-ratio
+/* Hash seed (randomised multipliers against adversarial keys; Eq. 4 fixes the golden-ratio
  * multiplier).  seed == 0 (the default): every table hash uses the
  * golden-ratio constants.  seed != 0: every later call (each sort, argsort,
  * batch launch or plan, server launch) draws its own odd 64-bit Eq. 4

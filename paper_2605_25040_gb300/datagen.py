@@ -173,7 +173,7 @@ def sorted_column(n: int, k: int, dtype=np.int64, seed: int = 0) -> np.ndarray:
     return np.sort(column(n, k, "uniform", dtype, seed))
 
 
-# Input profiles (SURVEY's input-profile row): runs of equal keys, one
+# Input profiles: runs of equal keys, one
 # contiguous group per key, and a nearly sorted column.
 
 def _group_sizes(n: int, k: int, seed: int) -> np.ndarray:
