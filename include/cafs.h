@@ -58,9 +58,11 @@ extern "C" {
  * width by an order-preserving bijection (unsigned: flip the sign bit; float:
  * flip the magnitude bits of negative values), sorts those, and maps the
  * output back, one extra elementwise read and write of the column each way.
- * cafs_sort, cafs_sort_ex, cafs_sort_host, cafs_estimate_k and cafs_argsort
- * accept every type; the batched, served and allocation-free entry points
- * take CAFS_INT32 and CAFS_INT64 only (else CAFS_ERR_UNSUPPORTED_DTYPE). */
+ * cafs_sort, cafs_sort_ex, cafs_sort_host, cafs_estimate_k, cafs_argsort,
+ * the batched form (per column: keys mapped into out before the launch,
+ * sorted there, mapped back after it) and the request server accept every
+ * type; the allocation-free entry point takes CAFS_INT32 and CAFS_INT64 only
+ * (else CAFS_ERR_UNSUPPORTED_DTYPE). */
 typedef enum {
   CAFS_INT32 = 0,
   CAFS_INT64 = 1,

@@ -338,8 +338,12 @@ def path_name(code: int) -> str:
 # ---------------------------------------------------------------------------
 # Batched form.
 # ---------------------------------------------------------------------------
-def _columns(keys_list, outs):
+def _columns(keys_list, outs, key_types=None):
+    """Column descriptors; ``key_types`` (optional, one name of KEY_TYPES or
+    None per column) reads a column's bits as that type."""
     n = len(keys_list)
+    if key_types is not None and len(key_types) != n:
+        raise ValueError("one key type per column")
     if outs is not None and len(outs) != n:
         raise ValueError("one output per column")
     arr = (Column * max(n, 1))()
@@ -353,7 +357,7 @@ def _columns(keys_list, outs):
         arr[i].keys = k.data_ptr() if k.numel() else None
         arr[i].out = o.data_ptr() if o.numel() else None
         arr[i].n = k.numel()
-        arr[i].dtype = _dtype_code(k.dtype)
+        arr[i].dtype = _key_code(k, key_types[i] if key_types is not None else None)
         arr[i].reserved = 0
     return arr
 
@@ -364,15 +368,17 @@ def default_tuning() -> dict:
     return t.as_dict()
 
 
-def sort_batch(keys_list, outs=None, tuning: dict | None = None, reports: bool = False, stream=None):
-    """Sorts many 1-D CUDA tensors with one batched launch.
+def sort_batch(keys_list, outs=None, tuning: dict | None = None, reports: bool = False, stream=None,
+               key_types=None):
+    """Sorts many 1-D CUDA tensors with one batched launch (``key_types``: an
+    optional key type name per column, as for ``sort``).
 
     Returns the outputs, and the per-column report dicts when ``reports``."""
     import torch
     lib = load()
     if outs is None:
         outs = [torch.empty_like(k) for k in keys_list]
-    arr = _columns(keys_list, outs)
+    arr = _columns(keys_list, outs, key_types)
     n = len(keys_list)
     reps = (Report * max(n, 1))() if reports else None
     t = BatchTuning.from_dict(tuning) if tuning else None
@@ -405,13 +411,13 @@ def time_tunings(keys_list, outs, tunings: list, reps: int = 3, stream=None) -> 
 class BatchPlan:
     """A recorded batched launch (CUDA graph) over fixed column buffers."""
 
-    def __init__(self, keys_list, outs, tuning: dict | None = None):
+    def __init__(self, keys_list, outs, tuning: dict | None = None, key_types=None):
         import torch
         self._lib = load()
         self.keys = list(keys_list)
         self.outs = list(outs)
         self.n = len(self.keys)
-        arr = _columns(self.keys, self.outs)
+        arr = _columns(self.keys, self.outs, key_types)
         t = BatchTuning.from_dict(tuning) if tuning else None
         h = ctypes.c_void_p()
         self.device = self.keys[0].device if self.n else torch.device("cuda", torch.cuda.current_device())

@@ -197,12 +197,10 @@ Workspace* workspace_for(int dev, cudaStream_t s) {
 
 // Key types: element width, the signed type the pipeline sorts (0: int32,
 // 1: int64) and the order map onto it (0: none, 1: unsigned, 2: IEEE float).
-bool known_type(cafs_dtype t) { return t >= CAFS_INT32 && t <= CAFS_FLOAT64; }
-size_t type_width(cafs_dtype t) { return (t == CAFS_INT64 || t == CAFS_UINT64 || t == CAFS_FLOAT64) ? 8 : 4; }
-int base_type(cafs_dtype t) { return type_width(t) == 8 ? 1 : 0; }
-int order_kind(cafs_dtype t) {
-  return (t == CAFS_UINT32 || t == CAFS_UINT64) ? 1 : (t == CAFS_FLOAT32 || t == CAFS_FLOAT64) ? 2 : 0;
-}
+bool known_type(cafs_dtype t) { return key_type_known(t); }
+size_t type_width(cafs_dtype t) { return key_type_width(t); }
+int base_type(cafs_dtype t) { return key_type_base(t); }
+int order_kind(cafs_dtype t) { return key_type_kind(t); }
 
 // `any_type`: the entry point takes every key type (else int32/int64 only).
 cafs_status check_args_impl(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out,
@@ -441,6 +439,9 @@ unsigned long long wait_timeout_ns() {
 }
 cafs_status check_args(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out) {
   return check_args_impl(keys, n, dtype, out, need_out);
+}
+cafs_status check_args_typed(const void* keys, size_t n, cafs_dtype dtype, const void* out, bool need_out) {
+  return check_args_impl(keys, n, dtype, out, need_out, true);
 }
 void fill_report(const Record& r, cafs_report* rep) { fill_report_impl(r, rep); }
 

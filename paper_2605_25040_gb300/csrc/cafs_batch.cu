@@ -23,6 +23,7 @@
 
 #include "cafs_batch_host.h"
 #include "cafs_phases.cuh"
+#include "cafs_transform.h"
 
 namespace cafs {
 
@@ -394,6 +395,7 @@ unsigned long long resolve_grid_min(const Tuning& t, unsigned long long total_ke
 
 cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t, int grid, Schedule* s) {
   s->cols.clear();
+  s->mapped.clear();
   s->grid_items.clear();
   s->cta_items.clear();
   s->n_max_grid = s->n_max_cta = s->sum_cta = 0;
@@ -405,7 +407,7 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
   for (size_t i = 0; i < ncols; ++i) {
     const cafs_column& c = cols[i];
     if (c.reserved != 0) return CAFS_ERR_INVALID_ARGUMENT;
-    cafs_status st = check_args(c.keys, c.n, c.dtype, c.out, true);
+    cafs_status st = check_args_typed(c.keys, c.n, c.dtype, c.out, true);
     if (st != CAFS_OK) return st;
     total += c.n;
   }
@@ -413,10 +415,13 @@ cafs_status make_schedule(const cafs_column* cols, size_t ncols, const Tuning& t
   for (size_t i = 0; i < ncols; ++i) {
     const cafs_column& c = cols[i];
     BatchColumn& b = s->cols[i];
-    b.keys = c.keys;
+    // unsigned and float columns: their signed images are sorted in place in out
+    const bool mapped = key_type_kind(c.dtype) != 0 && c.n != 0;
+    if (mapped) s->mapped.push_back(Schedule::Mapped{c.keys, c.out, (unsigned long long)c.n, c.dtype});
+    b.keys = mapped ? c.out : c.keys;
     b.out = c.out;
     b.n = c.n;
-    b.dtype = c.dtype == CAFS_INT64 ? 1 : 0;
+    b.dtype = (unsigned)key_type_base(c.dtype);
     b.pad = 0;
     if (c.n == 0) continue;
     if ((unsigned long long)c.n >= grid_min) {
@@ -579,6 +584,11 @@ cafs_status enqueue_batch(const BatchBuffers* b, const Schedule& sc, const Tunin
                           cudaStream_t s, bool count, unsigned* launched) {
   const size_t ncols = sc.cols.size();
   unsigned nl = 0;
+  for (const Schedule::Mapped& m : sc.mapped) {   // signed images of unsigned / float keys
+    if (launch_order_map(m.keys, m.out, m.n, (int)key_type_width(m.type), key_type_kind(m.type), s) != cudaSuccess)
+      return CAFS_ERR_CUDA;
+    ++nl;
+  }
   if (cudaMemsetAsync(b->d_state, 0, 2 * sizeof(BatchState), s) != cudaSuccess) return CAFS_ERR_CUDA;
   if (ncols && cudaMemsetAsync(b->d_records, 0, ncols * sizeof(Record), s) != cudaSuccess) return CAFS_ERR_CUDA;
   for (int dtype = 0; dtype < 2; ++dtype) {
@@ -587,6 +597,11 @@ cafs_status enqueue_batch(const BatchBuffers* b, const Schedule& sc, const Tunin
     // the grid barrier's words start from zero in every launch
     if (cudaMemsetAsync(b->grid_slot + b->gl.ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
     if (launch_batch(bp, dtype, grid, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    ++nl;
+  }
+  for (const Schedule::Mapped& m : sc.mapped) {   // the sorted images back to keys
+    if (launch_order_map(m.out, m.out, m.n, (int)key_type_width(m.type), key_type_kind(m.type), s) != cudaSuccess)
+      return CAFS_ERR_CUDA;
     ++nl;
   }
   if (count) count_launches(nl);

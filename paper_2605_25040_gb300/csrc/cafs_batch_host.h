@@ -50,6 +50,16 @@ struct BatchDevice {
 // The columns of one batch, validated and scheduled.
 struct Schedule {
   std::vector<BatchColumn> cols;
+  // Unsigned and float columns: their keys are mapped into `out` before the
+  // launch, the kernels sort those signed images in place, and `out` is
+  // mapped back after it.
+  struct Mapped {
+    const void* keys;
+    void* out;
+    unsigned long long n;
+    cafs_dtype type;
+  };
+  std::vector<Mapped> mapped;
   std::vector<unsigned> grid_items, cta_items;
   unsigned long long n_max_grid = 0, n_max_cta = 0;
   unsigned long long sum_cta = 0;   // keys in the per-CTA queue

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "cafs_batch_host.h"
+#include "cafs_transform.h"
 
 namespace cafs {
 namespace {
@@ -152,6 +153,12 @@ cafs_status enqueue_solo(cafs_server* sv, Request* r, Launch* L) {
   void* d = sv->arena_base + r->off;
   cudaStream_t s = sv->s_run;
   if (cudaMemcpyAsync(d, r->host_in, r->bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return CAFS_ERR_CUDA;
+  const int kind = key_type_kind(r->dtype);   // unsigned / float keys: sorted as signed images
+  const int width = (int)key_type_width(r->dtype);
+  if (kind) {
+    if (launch_order_map(d, d, r->n, width, kind, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    count_launches(1);
+  }
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(slot + gl.ctrl);
   if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
   Params p;
@@ -182,7 +189,7 @@ cafs_status enqueue_solo(cafs_server* sv, Request* r, Launch* L) {
   p.emit_tile_vec = sv->tuning.emit_tile_vec;
   p.timeout_ns = wait_timeout_ns();
   next_hash_multipliers(&p.hash_mult, &p.local_mult);
-  const int dtype = r->dtype == CAFS_INT64 ? 1 : 0;
+  const int dtype = key_type_base(r->dtype);
   cudaError_t e;
   if (r->n < kSmallN) {
     e = launch_small(p, dtype, s);
@@ -195,6 +202,10 @@ cafs_status enqueue_solo(cafs_server* sv, Request* r, Launch* L) {
   }
   if (e != cudaSuccess) return CAFS_ERR_CUDA;
   count_launches(1);
+  if (kind) {
+    if (launch_order_map(d, d, r->n, width, kind, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    count_launches(1);
+  }
   std::memset(L->h_state, 0, 2 * sizeof(BatchState));   // no batch state: both key types OK
   // The copy out goes on its own stream, as in the batched path, so that a
   // batch formed meanwhile does not wait behind it.
@@ -467,11 +478,11 @@ namespace {
 cafs_status submit_at(cafs_server* sv, const void* host_keys, size_t n, cafs_dtype dtype, void* host_out,
                       double t_arrival, uint64_t* ticket) {
   if (!sv || !ticket) return CAFS_ERR_INVALID_ARGUMENT;
-  cafs_status st = check_args(host_keys, n, dtype, host_out, false);
+  cafs_status st = check_args_typed(host_keys, n, dtype, host_out, false);
   if (st != CAFS_OK) return st;
   if (n && !host_out) return CAFS_ERR_INVALID_ARGUMENT;
   if ((unsigned long long)n > sv->max_request_keys) return CAFS_ERR_TOO_LARGE;
-  const unsigned long long bytes = (unsigned long long)n * (dtype == CAFS_INT64 ? 8 : 4);
+  const unsigned long long bytes = (unsigned long long)n * key_type_width(dtype);
   if (((bytes + kArenaAlign - 1) & ~(kArenaAlign - 1)) > sv->arena.size()) return CAFS_ERR_TOO_LARGE;
   Launch* direct = nullptr;
   Request* r = new Request();
@@ -589,7 +600,7 @@ cafs_status cafs_server_run_trace(cafs_server* sv, const cafs_request* reqs, siz
   for (size_t i = 0; i < nreq; ++i) {
     if (reqs[i].reserved != 0 || !(arrival_s[i] >= 0.0) || (i && arrival_s[i] < arrival_s[i - 1]))
       return CAFS_ERR_INVALID_ARGUMENT;
-    const cafs_status st = check_args(reqs[i].host_keys, reqs[i].n, reqs[i].dtype, reqs[i].host_out, false);
+    const cafs_status st = check_args_typed(reqs[i].host_keys, reqs[i].n, reqs[i].dtype, reqs[i].host_out, false);
     if (st != CAFS_OK) return st;
     if (reqs[i].n && !reqs[i].host_out) return CAFS_ERR_INVALID_ARGUMENT;
     if ((unsigned long long)reqs[i].n > sv->max_request_keys) return CAFS_ERR_TOO_LARGE;

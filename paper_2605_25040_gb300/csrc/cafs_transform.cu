@@ -62,6 +62,13 @@ cudaError_t launch_typed(const void* src, void* dst, unsigned long long n, int k
 
 }  // namespace
 
+bool key_type_known(cafs_dtype t) { return t >= CAFS_INT32 && t <= CAFS_FLOAT64; }
+size_t key_type_width(cafs_dtype t) { return (t == CAFS_INT64 || t == CAFS_UINT64 || t == CAFS_FLOAT64) ? 8 : 4; }
+int key_type_base(cafs_dtype t) { return key_type_width(t) == 8 ? 1 : 0; }
+int key_type_kind(cafs_dtype t) {
+  return (t == CAFS_UINT32 || t == CAFS_UINT64) ? 1 : (t == CAFS_FLOAT32 || t == CAFS_FLOAT64) ? 2 : 0;
+}
+
 cudaError_t launch_order_map(const void* src, void* dst, unsigned long long n, int width, int kind,
                              cudaStream_t s) {
   if (n == 0) return cudaSuccess;

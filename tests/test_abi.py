@@ -86,12 +86,16 @@ def test_key_types(lib):
     assert lib.cafs_sort(p + 4, 4, cafs.UINT64, p + 64, None) == 1
     assert lib.cafs_sort(p + 4, 4, cafs.FLOAT64, p + 64, None) == 1
     assert lib.cafs_sort(p, 8, cafs.FLOAT32, p + 4, None) == 4
-    # the allocation-free, batched and served entry points take int32/int64 only
+    # the allocation-free entry point takes int32/int64 only; the batched form
+    # checks every column's type (6 is no type)
     for t in (cafs.UINT32, cafs.UINT64, cafs.FLOAT32, cafs.FLOAT64):
         assert lib.cafs_sort_noalloc(p, 4, t, p + 64, None) == 2
-        cols = (cafs.Column * 1)()
-        cols[0].keys, cols[0].out, cols[0].n, cols[0].dtype = p, p + 256, 8, t
-        assert lib.cafs_sort_batch(cols, 1, None, None) == 2
+    cols = (cafs.Column * 1)()
+    cols[0].keys, cols[0].out, cols[0].n, cols[0].dtype = p, p + 256, 8, 6
+    assert lib.cafs_sort_batch(cols, 1, None, None) == 2
+    cols[0].dtype = cafs.FLOAT64
+    cols[0].keys = p + 4                       # misaligned 8-byte keys
+    assert lib.cafs_sort_batch(cols, 1, None, None) == 1
     assert cafs.KEY_TYPES["float64"] == (cafs.FLOAT64, 8)
 
 
@@ -108,7 +112,7 @@ def test_batch_argument_errors_are_synchronous(lib):
     p = ctypes.addressof(buf)
     cols = (cafs.Column * 2)()
     cols[0].keys, cols[0].out, cols[0].n, cols[0].dtype = p, p + 256, 8, cafs.INT64
-    cols[1].keys, cols[1].out, cols[1].n, cols[1].dtype = p + 128, p + 128, 8, 5
+    cols[1].keys, cols[1].out, cols[1].n, cols[1].dtype = p + 128, p + 128, 8, 6
     # an unsupported dtype in any column rejects the whole batch before any work
     assert lib.cafs_sort_batch(cols, 2, None, None) == 2
     cols[1].dtype = cafs.INT64

@@ -99,3 +99,60 @@ def test_lengths_sorted_and_host(dtype):
     xt = to_device(x)
     cafs.sort(xt, out=xt, key_type=np.dtype(dtype).name)
     assert np.array_equal(xt.cpu().numpy().view(np.uint8), O.frequency_sort_any(x).view(np.uint8))
+
+
+def mixed_type_columns():
+    cols = []
+    specs = [(np.uint32, 300_000, 5), (np.float32, 200_000, 200), (np.uint64, 250_000, 4096),
+             (np.float64, 300_000, 300_000), (np.uint64, 1500, 700), (np.float64, 100_000, 8),
+             (np.int64, 200_000, 50), (np.float32, 3000, 3000)]
+    for i, (dt, n, k) in enumerate(specs):
+        if np.dtype(dt).kind == "f":
+            cols.append(float_palette(k, dt, seed=i)[np.random.default_rng(i).integers(0, k, n)])
+        elif np.dtype(dt).kind == "u":
+            cols.append(G.column(n, k, "zipf", BITS[np.dtype(dt)], seed=i).view(dt))
+        else:
+            cols.append(G.column(n, k, "uniform", dt, seed=i))
+    return cols
+
+
+@pytest.mark.parametrize("tuning", [None, {"grid_min_n": 2048}])
+def test_batch_of_mixed_key_types(tuning):
+    cols = mixed_type_columns()
+    keys = [torch.from_numpy(x.view(BITS.get(x.dtype, x.dtype))).cuda() for x in cols]
+    names = [x.dtype.name for x in cols]
+    outs, reps = cafs.sort_batch(keys, reports=True, tuning=tuning, key_types=names)
+    for x, o, r in zip(cols, outs, reps):
+        assert np.array_equal(o.cpu().numpy().view(np.uint8), O.frequency_sort_any(x).view(np.uint8)), x.dtype
+        assert r["path"] == O.final_path_any(x)
+    # a recorded plan over the same buffers, refilled
+    outs2 = [torch.empty_like(k) for k in keys]
+    plan = cafs.BatchPlan(keys, outs2, key_types=names)
+    try:
+        for _ in range(2):
+            plan.launch()
+        torch.cuda.synchronize()
+        for x, o in zip(cols, outs2):
+            assert np.array_equal(o.cpu().numpy().view(np.uint8), O.frequency_sort_any(x).view(np.uint8))
+    finally:
+        plan.close()
+
+
+def test_server_key_types():
+    cols = mixed_type_columns()
+    srv = cafs.Server(2 << 30)
+    try:
+        outs = [np.empty_like(x) for x in cols]
+        tickets = [srv.submit(x, o) for x, o in zip(cols, outs)]
+        for x, o, t in zip(cols, outs, tickets):
+            rep, _ = srv.wait(t)
+            assert rep["device_status"] == 0
+            assert np.array_equal(o.view(np.uint8), O.frequency_sort_any(x).view(np.uint8)), x.dtype
+            assert rep["path"] == O.final_path_any(x)
+        # one at a time: the idle server's direct path
+        for x in cols[:3]:
+            o = np.empty_like(x)
+            rep, _ = srv.wait(srv.submit(x, o))
+            assert np.array_equal(o.view(np.uint8), O.frequency_sort_any(x).view(np.uint8))
+    finally:
+        srv.close()
