@@ -206,7 +206,8 @@ typedef struct {
   const void* keys;    /* device pointer, n elements                        */
   void* out;           /* device pointer, n elements; may equal keys        */
   size_t n;
-  cafs_dtype dtype;
+  cafs_dtype dtype;    /* any key type; unsigned and float keys are mapped
+                          into out before the launch and back after it      */
   int32_t reserved;    /* must be 0                                          */
 } cafs_column;
 
