@@ -404,6 +404,20 @@ def sweep_config(n: int, ncol: int, world: int) -> dict:
             "parallelism": f"replicas x{world}"}
 
 
+def replica_throughput(elapsed_ms: float, keys_per_rank: int, dist=None, device="cpu"):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    (all-reduce MAX of one scalar, no data-path collective) and every rank's
+    keys over it.  Returns (max elapsed ms, Gkeys/s)."""
+    world = 1
+    if dist is not None:
+        import torch
+        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+        world = dist.get_world_size()
+    return elapsed_ms, keys_per_rank * world / (elapsed_ms / 1e3) / 1e9
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on the host cores, bounded per step."""
     n = args.n
@@ -527,13 +541,7 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if dist:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-    total_keys = n * ncol * args.steps * world
-    value = total_keys / (elapsed_ms / 1e3) / 1e9
+    elapsed_ms, value = replica_throughput(t_start.elapsed_time(t_end), n * ncol * args.steps, dist, "cuda")
 
     # per-column device times (mean over timed steps)
     col_ms = [statistics.mean(events[s][i][0].elapsed_time(events[s][i][1]) for s in range(args.steps))
