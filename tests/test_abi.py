@@ -183,3 +183,18 @@ def test_workload_signature():
     from paper_2605_25040_gb300 import autotune
     keys = [torch.zeros(1000, dtype=torch.int64), torch.zeros(70000, dtype=torch.int32)]
     assert autotune.workload_signature(keys) == "cols=2:i32=1:log2n=[9,16]:log2sum=16"
+
+
+def test_binding_key_type_names():
+    import numpy as np
+    import torch
+    assert cafs._dtype_code(np.uint32) == cafs.UINT32 and cafs._dtype_code(np.float64) == cafs.FLOAT64
+    assert cafs._dtype_code(torch.float32) == cafs.FLOAT32 and cafs._dtype_code(torch.int64) == cafs.INT64
+    with pytest.raises(TypeError):
+        cafs._dtype_code(np.int16)
+    t64 = torch.zeros(4, dtype=torch.int64)
+    assert cafs._key_code(t64, "uint64") == cafs.UINT64 and cafs._key_code(t64, None) == cafs.INT64
+    with pytest.raises(ValueError):
+        cafs._key_code(t64, "float32")            # 4-byte type read from 8-byte elements
+    with pytest.raises(KeyError):
+        cafs._key_code(t64, "int8")
