@@ -20,7 +20,10 @@
  *              L = C/2 (an order-independent restatement of the paper's
  *              insertion-order-dependent spill test).
  *
- * Keys are signed two's-complement int32 or int64, sorted ascending.
+ * Keys are signed two's-complement int32 or int64 sorted ascending (the
+ * paper's Sec. 5 types); unsigned and IEEE-float keys are accepted too (see
+ * cafs_dtype).  Beyond the paper: a stable argsort (Sec. 3.1's permutation),
+ * a batched form, a request server and per-call hash seeds.
  *
  * Conventions shared by every entry point:
  *   - Device pointers are caller-owned CUDA device (or managed) memory of n
