@@ -327,3 +327,25 @@ def test_datagen_is_deterministic_and_shaped():
     assert c.dtype == np.int32 and np.unique(c).size == 50
     p = G.paper_palette(5000, 40)
     assert np.unique(p).size <= 40
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64, np.uint32, np.uint64, np.float32, np.float64])
+def test_any_type_degenerate_inputs(dtype):
+    empty = np.zeros(0, dtype=dtype)
+    assert O.frequency_sort_any(empty).size == 0 and O.stable_argsort_any(empty).size == 0
+    assert O.final_path_any(empty) == O.EMPTY
+    one = np.ones(1, dtype=dtype)
+    assert O.frequency_sort_any(one).tolist() == [1] and O.stable_argsort_any(one).tolist() == [0]
+    same = np.full(3000, 7, dtype=dtype)
+    assert O.final_path_any(same) == O.BYPASS_SORTED
+    assert np.array_equal(O.stable_argsort_any(same), np.arange(3000, dtype=np.uint32))
+
+
+@pytest.mark.parametrize("fdt,idt", [(np.float32, np.uint32), (np.float64, np.uint64)])
+def test_signed_zeros_are_two_keys(fdt, idt):
+    # equal keys are equal bit patterns: -0 sorts before +0, each group stable
+    x = np.array([0.0, -0.0, 0.0, -0.0, 1.0, -1.0], dtype=fdt)
+    got = O.frequency_sort_any(x).view(idt)
+    want = np.array([-1.0, -0.0, -0.0, 0.0, 0.0, 1.0], dtype=fdt).view(idt)
+    assert np.array_equal(got, want)
+    assert O.stable_argsort_any(x).tolist() == [5, 1, 3, 0, 2, 4]
