@@ -182,7 +182,32 @@ def cpu_baseline(columns, budget_s: float = 12.0) -> dict:
     names = ", ".join(n for n, _ in columns)
     return {"value": keys / t / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
             "sample": f"{runs} sorts of N={columns[0][1].size} sweep columns taken in turn from ({names}), "
-                      f"{t:.1f} s of numpy count-then-emit (single-threaded)"}
+                      f"{t:.1f} s of numpy count-then-emit (single-threaded)",
+            **host_cpu()}
+
+
+def host_cpu() -> dict:
+    """The host the CPU legs ran on: logical CPUs and the model name."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
 def _time_ms(torch, fn, warmup=2, reps=5):
@@ -337,6 +362,81 @@ def bench_profiles(torch, cafs, n, peak):
     return res
 
 
+MID_K = [10_000, 30_000, 100_000]
+
+
+def bench_mid_k(torch, cafs, n, peak):
+    """The hash-count path between one CTA's shared table and K = 1e5 (the
+    paper's operating range, Sec. 7.1): N = 3e7 int64, K in {1e4, 3e4, 1e5}
+    with uniform and Zipf(1.1) frequencies; per column the branch, the phase
+    split from the device timeline and the fraction of the HBM roofline."""
+    from paper_2605_25040_gb300 import datagen as G
+    res = {"timing": "CUDA events on the current stream, median of 5 after 2 warm-ups; inputs larger than L2",
+           "algorithmic_bytes_per_key": 16, "columns": []}
+    ok_all = True
+    for dist, base in (("uniform", 1000), ("zipf", 2000)):
+        for k in MID_K:
+            x = G.column_torch(n, k, dist, np.int64, seed=base + k, device="cuda")
+            out = torch.empty_like(x)
+            ms, ms_min = _time_ms(torch, lambda: cafs.sort(x, out))
+            _, rep = cafs.sort_ex(x, out)
+            ok_all &= bool(torch.equal(torch.sort(x).values, out))
+            tl = rep["timeline_ns"]
+            phases, prev = {}, tl[0]
+            for idx, nm in ((1, "sample"), (2, "monotone"), (3, "count"), (4, "pairs"),
+                            (5, "finish")):
+                if tl[idx]:
+                    phases[nm] = round((tl[idx] - prev) / 1e3, 1)
+                    prev = tl[idx]
+            res["columns"].append({"column": f"{dist}_K{k}", "path": cafs.path_name(rep["path"]),
+                                   "k_hat": rep["est"]["k_hat"], "k_distinct": rep["k_distinct"],
+                                   "ms": round(ms, 4), "min_ms": round(ms_min, 4), "phases_us": phases,
+                                   "gkeys_s": round(n / (ms / 1e3) / 1e9, 2),
+                                   "frac_hbm": round(16 * n / (ms / 1e3) / 1e9 / peak, 4)})
+            del x, out
+    res["verified_vs_torch_sort"] = ok_all
+    torch.cuda.empty_cache()
+    return res
+
+
+def hash_count_summary(sweep, mid_k, specs, bytes_per_col, peak):
+    """The count-and-emit columns (tiny or main branch) with K <= 1e5 of the
+    sweep and of the mid-K leg: their combined and worst fraction of the
+    HBM roofline (the target range of the hash-count path)."""
+    cols = []
+    for row, spec in zip(sweep, specs):
+        if spec["K"] is not None and spec["K"] <= 100_000 and row["path"] in ("tiny", "main", "tiny_miss_main"):
+            cols.append((row["column"], row["ms"]))
+    for row in (mid_k or {}).get("columns", []):
+        if row["path"] in ("tiny", "main", "tiny_miss_main"):
+            cols.append(("mid_" + row["column"], row["ms"]))
+    if not cols:
+        return None
+    tot_ms = sum(ms for _, ms in cols)
+    ach = bytes_per_col * len(cols) / (tot_ms / 1e3) / 1e9
+    worst = max(cols, key=lambda c: c[1])
+    return {"achieved": ach, "frac": ach / peak, "columns": [c for c, _ in cols],
+            "worst_column": worst[0], "worst_frac": bytes_per_col / (worst[1] / 1e3) / 1e9 / peak}
+
+
+def host_link(torch, nbytes=1 << 30, reps=5):
+    """Pinned host <-> device copy bandwidth (GB/s), one cudaMemcpyAsync per
+    buffer, CUDA events on the current stream: the ceiling of every figure
+    that moves keys through host memory."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, fn in (("h2d_gbs", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h_gbs", lambda: h.copy_(d, non_blocking=True))):
+        ms, _ = _time_ms(torch, fn, warmup=2, reps=reps)
+        out[name] = round(nbytes / (ms / 1e3) / 1e9, 1)
+    out["bytes_per_copy"] = nbytes
+    out["method"] = "pinned torch tensors, one copy per direction, median of 5 after 2 warm-ups"
+    del h, d
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_batched(torch, cafs):
     from paper_2605_25040_gb300 import datagen as G
     res = {}
@@ -449,7 +549,7 @@ def run_reference(args, rank, world):
         "config": sweep_config(n, len(cols), world),
         "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step sorts {per_step} of the {len(cols)} sweep columns (full N), "
-                                   "taken in turn; value = their keys / their CPU time"},
+                                   "taken in turn; value = their keys / their CPU time", **host_cpu()},
         "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -469,6 +569,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-form measurement")
+    ap.add_argument("--no-mid-k", action="store_true", help="skip the mid-K (1e4..1e5) hash-count leg")
     ap.add_argument("--no-argsort", action="store_true",
                     help="skip the argsort, key-type and input-profile measurements")
     ap.add_argument("--columns", default="",
@@ -565,7 +666,8 @@ def main():
         tl = rep["timeline_ns"]
         phases = {}
         prev = tl[0]
-        for idx, nm in ((1, "sample"), (2, "monotone"), (3, "count"), (4, "pairs"), (5, "finish")):
+        for idx, nm in ((1, "sample"), (2, "monotone"), (3, "count"), (4, "pairs"),
+                        (5, "finish")):
             if tl[idx]:
                 phases[nm] = round((tl[idx] - prev) / 1e3, 1)
                 prev = tl[idx]
@@ -611,6 +713,18 @@ def main():
                       "of different columns overlap)",
                "blocking_per_column": {"value": n * ncol * e2e_steps * world / dt_blocking / 1e9,
                                        "api": "cafs_sort_host, one column at a time"}}
+
+    mid_k = link = None
+    if rank == 0 and not args.no_mid_k and n == 30_000_000:
+        mid_k = bench_mid_k(torch, cafs, n, peak)
+    if rank == 0 and not args.no_e2e:
+        link = host_link(torch)
+        if e2e is not None:
+            e2e["host_link"] = link
+            # each key crosses the link twice (in and out); the copies of one
+            # column overlap the other direction's, so the tighter of the two
+            # one-way ceilings bounds the overlapped figure
+            e2e["host_link_ceiling_gkeys_s"] = round(min(link["h2d_gbs"], link["d2h_gbs"]) / 8, 2)
 
     argsort = key_types = profiles = None
     if rank == 0 and not args.no_argsort:
@@ -659,12 +773,15 @@ def main():
                      "main_path_K_le_1e5": {"achieved": main_ach, "frac": main_ach / peak,
                                             "traffic": traffic["main_path_mean_dram_bytes_per_launch"]
                                             if traffic else None,
-                                            "columns": [specs[i]["name"] for i in main_idx]}},
+                                            "columns": [specs[i]["name"] for i in main_idx]},
+                     "hash_count_K_le_1e5": hash_count_summary(sweep, mid_k, specs, bytes_per_col, peak)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
         "sweep": sweep,
+        "mid_k": mid_k,
+        "host_link": link,
         "batched": batched,
         "served": served,
         "argsort": argsort,

@@ -194,13 +194,24 @@ constexpr unsigned long long pair_capacity(unsigned long long tcap) {
   return tcap / 2 + 2 > (unsigned long long)kSmallPairs ? tcap / 2 + 2 : (unsigned long long)kSmallPairs;
 }
 
+// The pair bucket sort (K' > kRankPairs) runs on grids of up to this many
+// CTAs; its scratch holds, per producer CTA and bucket, a pair count, a key
+// count sum and a base (three G x G arrays of 32-bit words), then the bucket
+// totals and their key-count sums (64-bit words).
+constexpr unsigned kBucketMaxGrid = 256;
+__host__ __device__ constexpr unsigned long long bucket_scratch_words(unsigned long long G) {
+  return (3ull * G * G + 2ull * G + 1ull) / 2ull + 1ull;
+}
+
 // 64-bit words of the radix scratch of a scope of `parts` CTAs: per-CTA
 // digit counts and bases, two [parts][kRadixDigits] arrays of 32-bit words,
+// then the pair bucket sort's scratch (grids up to kBucketMaxGrid CTAs),
 // then the grid-wide sampler's kSamples gathered keys in the last kSamples
 // words (apart, because a CTA may start counting digits while another still
 // reads the samples).
 constexpr unsigned long long radix_scratch_words(unsigned long long parts) {
-  return parts * kRadixDigits + (unsigned long long)kSamples;
+  return parts * kRadixDigits + bucket_scratch_words(parts < kBucketMaxGrid ? parts : kBucketMaxGrid) +
+         (unsigned long long)kSamples;
 }
 
 // The same for any grid up to kMaxGrid (independent of n).

@@ -1434,6 +1434,233 @@ __device__ bool grid_scan_counts(const Params& p, const unsigned* vals, unsigned
   return sc.sync(c, epoch, p.timeout_ns);
 }
 
+// How a column's pass through column_body() ended.
+enum ColumnEnd : int {
+  kColumnDone = 0,     // output written
+  kColumnRadix = 1,    // the path ends in the LSD radix fallback, not yet run
+  kColumnFailed = 2,   // a bounded wait gave up; the status is in the record
+  kColumnTooBig = 3,   // the Eq. 6 table exceeds this workspace's table; nothing
+                       // was counted (only the sampler's record was written)
+};
+
+// ---------------------------------------------------------------------------
+// Phase 3b (K' > kRankPairs, all CTAs of a grid): splitter bucket sort of the
+// pairs, the sort and exclusive scan of Alg. 4 without a radix pass.
+//   1. the claimed slots are gathered into the pair arrays A (the table is
+//      reset on the way);
+//   2. every CTA sorts the same evenly spaced sample of A's keys in shared
+//      memory and takes G - 1 splitters from it, so bucket g (owned by CTA g)
+//      holds a contiguous key range; every CTA counts its share of the pairs
+//      per bucket (and the key counts they carry);
+//   3. CTA g scans bucket g's counts over the producing CTAs;
+//   4. every CTA scatters its share into the buckets (array B);
+//   5. CTA g sorts bucket g in shared memory and writes its keys and run
+//      offsets (bucket starts and count starts are exclusive scans of the
+//      bucket totals, which every CTA computes).
+// Keys are distinct, so the order inside a bucket before step 5 does not
+// matter.  Five grid barriers in all.  Returns kColumnFailed on a failed
+// barrier, kColumnRadix when a bucket is too large for one CTA (the caller
+// then sorts A with the radix sort), kColumnDone otherwise.
+// ---------------------------------------------------------------------------
+constexpr int kBucketSortCap = 16384;   // pairs one CTA sorts in shared memory
+constexpr int kPairSamplesPerCta = 16;
+constexpr int kPairSamplesMax = 4096;
+static_assert(kBucketSortCap * 12 <= kPipelineSmem, "bucket in shared memory");
+
+// Number of splitters <= x among spl[0, P - 1) (P a power of two, entries
+// past the G - 1 splitters hold LLONG_MAX), clamped to the last bucket.
+__device__ __forceinline__ unsigned bucket_of(const long long* spl, int P, long long x, unsigned G) {
+  int pos = 0;
+  for (int step = P >> 1; step >= 1; step >>= 1)
+    if (spl[pos + step - 1] <= x) pos += step;
+  return (unsigned)pos < G ? (unsigned)pos : G - 1u;
+}
+
+// In-place ascending bitonic sort of n (a power of two) pairs by key, by all
+// threads; entries with value 0 (padding) sort after real entries (values
+// >= 1) of an equal key.
+__device__ __forceinline__ void bitonic_sort_counted(long long* k, unsigned* v, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const long long a = k[i], b = k[j];
+          const unsigned va = v[i], vb = v[j];
+          const bool a_gt = a > b || (a == b && va == 0u && vb != 0u);
+          if (a_gt == up) {
+            k[i] = b; k[j] = a;
+            v[i] = vb; v[j] = va;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The bucket sort's scratch in p.lookback starts after the radix sort's
+// per-CTA digit counts and bases (G x 256 64-bit words), which the radix
+// fallback of the pairs writes while other CTAs may still read it.
+__device__ __forceinline__ bool bucket_sort_fits(const Params& p, unsigned G) {
+  return G <= (unsigned)kBucketMaxGrid &&
+         (unsigned long long)G * kRadixDigits + bucket_scratch_words(G) + kSamples <= p.lookback_cap;
+}
+
+template <typename K>
+__device__ int phase_bucket_pairs(const Params& p, unsigned occ, unsigned long long special,
+                                  unsigned long long kp, unsigned char* smem, unsigned& epoch,
+                                  const GridScope& sc) {
+  using T = KeyTraits<K>;
+  Ctrl* c = p.ctrl;
+  const unsigned G = sc.nparts(), b = sc.part();
+  K* ak = reinterpret_cast<K*>(p.pkeys_a);
+  unsigned* av = p.pvals_a;
+  K* bk = reinterpret_cast<K*>(p.pkeys_b);
+  unsigned* bv = p.pvals_b;
+
+  // 1. gather + reset
+  {
+    const unsigned long long Gt = sc.gthreads(), gt = sc.gthread();
+    for (unsigned long long i = gt; i < occ; i += Gt) {
+      const unsigned slot = __ldcg(p.claimed + i);
+      ak[i] = (K)(long long)__ldcg(p.tkeys + slot);
+      av[i] = __ldcg(p.tcounts + slot);
+      p.tkeys[slot] = kEmpty64;
+      p.tcounts[slot] = 0u;
+    }
+    if (special && gt == 0) {
+      ak[occ] = T::min_key();
+      av[occ] = (unsigned)special;
+    }
+  }
+  if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+
+  unsigned* cnt = reinterpret_cast<unsigned*>(p.lookback + (size_t)G * kRadixDigits);   // [G][G] pairs of b' in g
+  unsigned* csm = cnt + (size_t)G * G;                        // [G][G] their key counts
+  unsigned* base = csm + (size_t)G * G;                       // [G][G] first position of b' in g
+  unsigned* tot = base + (size_t)G * G;                       // [G]
+  unsigned* tsum = tot + G;                                   // [G]
+
+  // 2. splitters and per-bucket counts of this CTA's share
+  const int P = (int)bit_ceil_u64(G);
+  long long* spl = reinterpret_cast<long long*>(smem);                          // P
+  unsigned* hcnt = reinterpret_cast<unsigned*>(spl + P);                        // P
+  unsigned* hsum = hcnt + P;                                                    // P
+  unsigned* aux = hsum + P;                                                     // kWarps + 8
+  long long* samp = reinterpret_cast<long long*>(smem + 32 * 1024);             // kPairSamplesMax
+  {
+    unsigned long long nsamp = (unsigned long long)kPairSamplesPerCta * G;
+    if (nsamp > (unsigned long long)kPairSamplesMax) nsamp = kPairSamplesMax;
+    if (nsamp > kp) nsamp = kp;
+    const int ps = (int)bit_ceil_u64(nsamp);
+    for (int j = threadIdx.x; j < ps; j += blockDim.x)
+      samp[j] = (unsigned long long)j < nsamp ? (long long)__ldcg(ak + (kp * (unsigned long long)j) / nsamp)
+                                              : LLONG_MAX;
+    for (int g = threadIdx.x; g < P; g += blockDim.x) {
+      hcnt[g] = 0u;
+      hsum[g] = 0u;
+    }
+    __syncthreads();
+    bitonic_sort_pairs(samp, nullptr, ps);
+    for (int g = threadIdx.x; g < P; g += blockDim.x)
+      spl[g] = (unsigned)g + 1u < G ? samp[((unsigned long long)(g + 1) * nsamp) / G] : LLONG_MAX;
+    __syncthreads();
+  }
+  const unsigned long long i0 = kp * b / G, i1 = kp * (b + 1) / G;
+  for (unsigned long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const unsigned g = bucket_of(spl, P, (long long)__ldcg(ak + i), G);
+    atomicAdd(hcnt + g, 1u);
+    atomicAdd(hsum + g, __ldcg(av + i));
+  }
+  __syncthreads();
+  for (unsigned g = threadIdx.x; g < G; g += blockDim.x) {
+    cnt[(size_t)b * G + g] = hcnt[g];
+    csm[(size_t)b * G + g] = hsum[g];
+  }
+  if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+
+  // 3. bucket b: exclusive scan of its counts over the producers
+  {
+    unsigned t = 0;
+    const unsigned v = threadIdx.x < G ? __ldcg(cnt + (size_t)threadIdx.x * G + b) : 0u;
+    const unsigned s = threadIdx.x < G ? __ldcg(csm + (size_t)threadIdx.x * G + b) : 0u;
+    const unsigned ex = block_exclusive_scan(v, aux, &t);
+    if (threadIdx.x < G) base[(size_t)threadIdx.x * G + b] = ex;
+    const unsigned ss = block_sum(s, aux);
+    if (threadIdx.x == 0) {
+      tot[b] = t;
+      tsum[b] = ss;
+    }
+  }
+  if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+
+  // bucket starts and count starts (every CTA); too large a bucket: radix
+  unsigned* bstart = hcnt;   // reuses the histogram arrays
+  unsigned* cstart = hsum;
+  unsigned* cur = aux + kWarps + 8;   // P cursors
+  {
+    unsigned t = 0;
+    const unsigned v = threadIdx.x < G ? __ldcg(tot + threadIdx.x) : 0u;
+    const unsigned s = threadIdx.x < G ? __ldcg(tsum + threadIdx.x) : 0u;
+    const int big = __syncthreads_or(v > (unsigned)kBucketSortCap);
+    const unsigned ex = block_exclusive_scan(v, aux, &t);
+    if (threadIdx.x < G) bstart[threadIdx.x] = ex;
+    const unsigned exs = block_exclusive_scan(s, aux, &t);
+    if (threadIdx.x < G) {
+      cstart[threadIdx.x] = exs;
+      cur[threadIdx.x] = ex + __ldcg(base + (size_t)b * G + threadIdx.x);
+    }
+    __syncthreads();
+    if (big) return kColumnRadix;
+  }
+
+  // 4. scatter this CTA's share into the buckets
+  for (unsigned long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const K x = __ldcg(ak + i);
+    const unsigned g = bucket_of(spl, P, (long long)x, G);
+    const unsigned pos = atomicAdd(cur + g, 1u);
+    bk[pos] = x;
+    bv[pos] = __ldcg(av + i);
+  }
+  const unsigned my_start = bstart[b], my_cstart = cstart[b];
+  __syncthreads();
+  if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+
+  // 5. sort bucket b in shared memory, write keys and run offsets
+  const unsigned m = __ldcg(tot + b);
+  if (m > 0) {
+    long long* sk = reinterpret_cast<long long*>(smem);
+    unsigned* sv = reinterpret_cast<unsigned*>(sk + kBucketSortCap);
+    const int pm = (int)bit_ceil_u64(m);
+    for (int j = threadIdx.x; j < pm; j += blockDim.x) {
+      const bool real = (unsigned)j < m;
+      sk[j] = real ? (long long)__ldcg(bk + my_start + j) : LLONG_MAX;
+      sv[j] = real ? __ldcg(bv + my_start + j) : 0u;
+    }
+    __syncthreads();
+    bitonic_sort_counted(sk, sv, pm);
+    K* skeys = reinterpret_cast<K*>(p.skeys);
+    unsigned long long carry = my_cstart;
+    unsigned long long* scan_scratch = reinterpret_cast<unsigned long long*>(sv + kBucketSortCap);
+    for (unsigned j0 = 0; j0 < m; j0 += blockDim.x) {
+      const unsigned j = j0 + threadIdx.x;
+      const unsigned long long v = j < m ? (unsigned long long)sv[j] : 0ull;
+      unsigned long long t;
+      const unsigned long long ex = block_exclusive_scan(v, scan_scratch, &t);
+      if (j < m) {
+        skeys[my_start + j] = (K)sk[j];
+        p.offsets[my_start + j] = (unsigned)(carry + ex);
+      }
+      carry += t;
+    }
+  }
+  if (b == 0 && threadIdx.x == 0) p.offsets[kp] = (unsigned)p.n;
+  if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
+  return kColumnDone;
+}
+
 // ---------------------------------------------------------------------------
 // Phase 4: emit.  Output tiles of p.emit_tile_vec 16-byte vectors; each CTA
 // looks up the first and last run of each of its tiles (binary search on the
@@ -1561,15 +1788,6 @@ __device__ __forceinline__ void mark(Ctrl* c, int i, const S& sc) {
   if (sc.lead()) c->rec.timeline[i] = global_timer_ns();
 }
 
-// How a column's pass through column_body() ended.
-enum ColumnEnd : int {
-  kColumnDone = 0,     // output written
-  kColumnRadix = 1,    // the path ends in the LSD radix fallback, not yet run
-  kColumnFailed = 2,   // a bounded wait gave up; the status is in the record
-  kColumnTooBig = 3,   // the Eq. 6 table exceeds this workspace's table; nothing
-                       // was counted (only the sampler's record was written)
-};
-
 // Algorithm 3 for one column of n >= 2048 keys, run by the CTAs of `sc`:
 // sample and estimate, the sortedness bypass, then the tiny or main count,
 // the pair sort and scan, and the emit.  A path that ends in the radix
@@ -1673,23 +1891,44 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
     if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
     mark(c, 4, sc);
     reset_claimed(p, occ, sc);
+    phase_emit<K>(p, kp, smem, sc);
+    return kColumnDone;
   } else {
-    // Gather the claimed slots into pair arrays and reset the table.
+    int pairs_end = kColumnRadix;   // the radix sort of the pairs, unless the bucket sort ran
+    if constexpr (kGrid) {
+      if (bucket_sort_fits(p, sc.nparts())) {
+        pairs_end = phase_bucket_pairs<K>(p, occ, special, kp, smem, epoch, sc);
+        if (pairs_end == kColumnFailed) return kColumnFailed;
+      }
+    }
+    if (pairs_end == kColumnDone) {
+      mark(c, 4, sc);
+      phase_emit<K>(p, kp, smem, sc);
+      return kColumnDone;
+    }
+  }
+  {
+    // Gather the claimed slots into pair arrays and reset the table (the
+    // bucket sort may have done so already), LSD radix, scan.
     K* ak = reinterpret_cast<K*>(p.pkeys_a);
     const unsigned long long G = sc.gthreads();
     const unsigned long long gt = sc.gthread();
-    for (unsigned long long i = gt; i < occ; i += G) {
-      const unsigned slot = __ldcg(p.claimed + i);
-      ak[i] = (K)(long long)__ldcg(p.tkeys + slot);
-      p.pvals_a[i] = __ldcg(p.tcounts + slot);
-      p.tkeys[slot] = kEmpty64;
-      p.tcounts[slot] = 0u;
+    bool gathered = false;
+    if constexpr (kGrid) gathered = bucket_sort_fits(p, sc.nparts());
+    if (!gathered) {
+      for (unsigned long long i = gt; i < occ; i += G) {
+        const unsigned slot = __ldcg(p.claimed + i);
+        ak[i] = (K)(long long)__ldcg(p.tkeys + slot);
+        p.pvals_a[i] = __ldcg(p.tcounts + slot);
+        p.tkeys[slot] = kEmpty64;
+        p.tcounts[slot] = 0u;
+      }
+      if (special && gt == 0) {
+        ak[occ] = KeyTraits<K>::min_key();
+        p.pvals_a[occ] = (unsigned)special;
+      }
+      if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
     }
-    if (special && gt == 0) {
-      ak[occ] = KeyTraits<K>::min_key();
-      p.pvals_a[occ] = (unsigned)special;
-    }
-    if (!sc.sync(c, epoch, p.timeout_ns)) return kColumnFailed;
     if (!radix_sort<K, true>(p, ak, p.pvals_a, kp, reinterpret_cast<K*>(p.skeys), p.svals,
                              reinterpret_cast<K*>(p.pkeys_b), p.pvals_b, smem, epoch, sc))
       return kColumnFailed;

@@ -35,11 +35,16 @@ def _device():
 
 
 @pytest.mark.parametrize("kind,k", [("uniform", 200), ("zipf", 4096), ("uniform", 4),
-                                    ("uniform", 130_000), ("uniform", N), ("spill", 0)])
+                                    ("uniform", 130_000), ("uniform", N), ("spill", 0),
+                                    ("mid_uniform", 10_000), ("mid_uniform", 100_000),
+                                    ("mid_zipf", 30_000)])
 def test_sweep_column_full_size(kind, k):
-    # the same columns (and seeds) as the benchmark's sweep
+    # the same columns (and seeds) as the benchmark's sweep and mid-K leg
     seed = {("uniform", 200): 3, ("zipf", 4096): 13, ("uniform", 4): 0, ("uniform", 130_000): 5,
-            ("uniform", N): 8, ("spill", 0): 18}[(kind, k)]
+            ("uniform", N): 8, ("spill", 0): 18, ("mid_uniform", 10_000): 1000 + 10_000,
+            ("mid_uniform", 100_000): 1000 + 100_000, ("mid_zipf", 30_000): 2000 + 30_000}[(kind, k)]
+    if kind.startswith("mid_"):
+        kind = kind[4:]
     if kind == "spill":
         xt = G.spill_trigger_torch(N, np.int64, seed=seed, device="cuda")
     else:
