@@ -63,7 +63,9 @@ struct Workspace {
   unsigned long long lookback_cap = 0;
   size_t io_bytes = 0;
   // device buffers
-  Ctrl* ctrl = nullptr;
+  Ctrl* ctrl = nullptr;        // two blocks: launch i uses ctrl[cur] and zeroes the other
+  int cur = 0;
+  Ctrl* last = nullptr;        // the block of the last launch (its record is the report)
   unsigned long long* tkeys = nullptr;
   unsigned* tcounts = nullptr;
   unsigned* claimed = nullptr;
@@ -139,7 +141,7 @@ cafs_status ensure_workspace(Workspace* w, unsigned long long n, int dtype, cuda
     const unsigned long long nlc = lcap > w->lookback_cap ? lcap : w->lookback_cap;
     const size_t ntb = tmp_bytes > w->tmp_bytes ? tmp_bytes : w->tmp_bytes;
     release_buffers(w);
-    bool ok = alloc(&w->ctrl, sizeof(Ctrl)) == cudaSuccess &&
+    bool ok = alloc(&w->ctrl, 2 * sizeof(Ctrl)) == cudaSuccess &&
               alloc(&w->tkeys, ntc * 8) == cudaSuccess &&
               alloc(&w->tcounts, ntc * 4) == cudaSuccess &&
               alloc(&w->claimed, ntc * 4) == cudaSuccess &&
@@ -163,6 +165,9 @@ cafs_status ensure_workspace(Workspace* w, unsigned long long n, int dtype, cuda
     g_launches++;
     if (cudaMemsetAsync(w->tcounts, 0, ntc * 4, s) != cudaSuccess) return CAFS_ERR_CUDA;
     if (cudaMemsetAsync(w->lookback, 0, nlc * 8, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    if (cudaMemsetAsync(w->ctrl, 0, 2 * sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
+    w->cur = 0;
+    w->last = w->ctrl;
     w->table_cap = ntc; w->pair_cap = npc; w->lookback_cap = nlc; w->tmp_bytes = ntb;
     w->n_cap = n;
   }
@@ -244,7 +249,8 @@ Params pipeline_params(Workspace* w, const void* keys, void* out, unsigned long 
   p.keys = keys;
   p.out = out;
   p.n = n;
-  p.ctrl = w->ctrl;
+  p.ctrl = w->ctrl + w->cur;
+  p.ctrl_next = w->ctrl + (w->cur ^ 1);
   p.tkeys = w->tkeys;
   p.tcounts = w->tcounts;
   p.claimed = w->claimed;
@@ -277,10 +283,18 @@ int launch_grid(unsigned long long n, int max_grid) {
   return grid < 1 ? 1 : (int)grid;
 }
 
-// Enqueues one pipeline run on stream s (g_mu held).
+// The launch just enqueued used ctrl[cur] and zeroes the other block: the
+// next launch takes that one (g_mu held).
+void advance_ctrl(Workspace* w) {
+  w->last = w->ctrl + w->cur;
+  w->cur ^= 1;
+}
+
+// Enqueues one pipeline run on stream s (g_mu held).  The control block it
+// uses was zeroed by the previous launch on this workspace (or at
+// allocation).
 cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* out,
                     unsigned long long n, int dtype, int mode, cudaStream_t s) {
-  if (cudaMemsetAsync(w->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
   const Params p = pipeline_params(w, keys, out, n, mode);
   cudaError_t e;
   if (n < kSmallN) {
@@ -289,12 +303,13 @@ cafs_status enqueue(Workspace* w, const DeviceInfo* d, const void* keys, void* o
     e = launch_pipeline(p, dtype, launch_grid(n, d->max_grid[dtype]), s);
   }
   if (e != cudaSuccess) return CAFS_ERR_CUDA;
+  advance_ctrl(w);
   g_launches++;
   return CAFS_OK;
 }
 
 cafs_status read_record(Workspace* w, cudaStream_t s, Record* r) {
-  if (cudaMemcpyAsync(w->host_rec, &w->ctrl->rec, sizeof(Record), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (cudaMemcpyAsync(w->host_rec, &w->last->rec, sizeof(Record), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return CAFS_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CAFS_ERR_CUDA;
   *r = *w->host_rec;
@@ -404,7 +419,6 @@ cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out
     if ((st = map_keys(keys, w->io, n, dtype, s)) != CAFS_OK) return st;
     src = w->io;
   }
-  if (cudaMemsetAsync(w->ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
   ArgsortParams ap;
   ap.p = pipeline_params(w, src, out, n, kModeSort);
   ap.perm = perm;
@@ -416,6 +430,7 @@ cafs_status argsort_impl(const void* keys, size_t n, cafs_dtype dtype, void* out
   if (n < kSmallN) e = launch_small_argsort(ap, bt, s);
   else e = launch_argsort(ap, bt, launch_grid(n, d->max_grid_arg[bt]), s);
   if (e != cudaSuccess) return CAFS_ERR_CUDA;
+  advance_ctrl(w);
   g_launches++;
   if (mapped && (st = map_keys(out, out, n, dtype, s)) != CAFS_OK) return st;
   if (report) {

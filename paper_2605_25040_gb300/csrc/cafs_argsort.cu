@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kThreads, 1) argsort_kernel(ArgsortParams ap) 
   const GridScope sc;
   const Params& p = ap.p;
   Ctrl* c = p.ctrl;
+  zero_next_ctrl(p);
   mark(c, 0, sc);
   unsigned epoch = 0;
   const int end = column_body<K>(p, smem, sc, epoch);
@@ -107,6 +108,7 @@ template <typename K>
 __global__ void __launch_bounds__(kThreads, 1) small_argsort_kernel(ArgsortParams ap) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Params& p = ap.p;
+  zero_next_ctrl(p);
   small_body<K>(p, smem);
   __syncthreads();
   const K* keys = reinterpret_cast<const K*>(p.keys);

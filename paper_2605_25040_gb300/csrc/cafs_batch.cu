@@ -37,6 +37,7 @@ __device__ __forceinline__ Params column_params(const BatchColumn& col, unsigned
   p.out = col.out;
   p.n = col.n;
   p.ctrl = reinterpret_cast<Ctrl*>(slot + L.ctrl);
+  p.ctrl_next = nullptr;
   p.tkeys = reinterpret_cast<unsigned long long*>(slot + L.tkeys);
   p.tcounts = reinterpret_cast<unsigned*>(slot + L.tcounts);
   p.claimed = reinterpret_cast<unsigned*>(slot + L.claimed);

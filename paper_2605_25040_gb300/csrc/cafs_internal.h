@@ -125,6 +125,9 @@ struct Params {
   void* out;
   unsigned long long n;
   Ctrl* ctrl;
+  // A second control block that CTA 0 zeroes at the start of the launch, for
+  // the launch after this one (nullptr: none; the host zeroes ctrl instead).
+  Ctrl* ctrl_next;
   // global hash table (C slots used, capacity table_cap)
   unsigned long long* tkeys;
   unsigned* tcounts;

@@ -549,12 +549,17 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
 // Phase 2: count (tiny or main).
 // ---------------------------------------------------------------------------
 
-// The CTA's shared counting table: NB buckets of kBucketSlots keys (16 bytes
-// of int32 keys or 32 bytes of int64 keys per bucket, Sec. 4.2's one-line
-// bucket), each slot with R counter replicas (lane % R) so that lanes of a
-// warp hitting the same key do not serialise.  Passed by value to the
-// non-inlined slow path so that the hot loop stays small.
-// Slots per bucket: one 16-byte shared-memory load reads a whole bucket.
+// The CTA's shared counting table: NB buckets of kBucketSlots keys (one
+// 16-byte shared-memory load reads a bucket: 4 int32 or 2 int64 keys, the
+// GPU form of Sec. 4.2's one-line bucket), each slot with R counter replicas
+// (lane % R) so that lanes of a warp hitting the same key do not serialise.
+// A key lives in one of two buckets, chosen by two multiplicative hashes of
+// its 32-bit fold: the lookup reads both with two independent loads, so that
+// every key costs the same (a probe sequence of data-dependent length makes
+// the whole warp wait for its longest one; measured 50 us for a column of
+// 3e7 keys in a table with every key in its first slot, 73-120 us with
+// linear probing).  Passed by value to the non-inlined slow path so that the
+// hot loop stays small.
 template <typename K>
 constexpr int bucket_slots() { return 16 / (int)sizeof(K); }
 
@@ -566,11 +571,15 @@ struct LocalTable {
   unsigned* occ;    // distinct keys held
   unsigned limit;   // at most this many distinct keys (half the slots)
   int logNB, NB, R, lane_rep;
-  unsigned mult;    // bucket-hash multiplier (odd)
+  unsigned mult;    // first bucket hash multiplier (odd); the second is derived
+  int two;          // 1: two-choice buckets; 0: linear probing over buckets
   GlobalTable gt;
 
-  __device__ __forceinline__ unsigned home(K x) const {
-    return local_bucket_m(fold32((typename KeyTraits<K>::U)x), mult, logNB);
+  __device__ __forceinline__ unsigned first(unsigned x32) const {
+    return local_bucket_m(x32, mult, logNB);
+  }
+  __device__ __forceinline__ unsigned second(unsigned x32) const {
+    return local_bucket_m(x32, (mult * 0xA3B195A5u) | 1u, logNB);
   }
   __device__ __forceinline__ void add(unsigned slot) const {
     atomicAdd(cnt + slot * R + lane_rep, 1u);
@@ -587,20 +596,26 @@ __device__ __forceinline__ void load_bucket(const int* kb, int* k) {
   k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
 }
 
-// Slow path of one key (not the type minimum) that is not in its home
-// bucket: scan buckets from home (linear probing over buckets); a key lives
-// in the first bucket that had a free slot when it was inserted, so the scan
-// stops at the first bucket with a free slot.  Claims that slot while the
-// table holds fewer than `limit` distinct keys, else goes to the global table.
-// `inc` is 0 when the table is being seeded with the sampled keys.
+// Slow path of one key (not the type minimum) that was not found by the
+// fast lookup: scan its buckets in a fixed order (two-choice: its first
+// bucket, then its second; otherwise linear probing over buckets from the
+// first) and claim the first empty slot while the table holds fewer than
+// `limit` distinct keys; otherwise (or when its buckets are full) count it in
+// the global table.  Slots are never emptied and always tried in the same
+// order, so a key occupies at most one slot: a later scan of it passes the
+// same occupied slots and meets it before any empty one.  `inc` is 0 when
+// the table is being seeded with the sampled keys.
 template <typename K>
 __device__ __forceinline__ void slow_insert(K x, const LocalTable<K>& t, unsigned inc) {
   using T = KeyTraits<K>;
   constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
   const K kmin = T::min_key();
   if (t.keys) {
-    unsigned b = t.home(x);
-    for (int probe = 0; probe < t.NB; ++probe, b = (b + 1) & (unsigned)(t.NB - 1)) {
+    const unsigned x32 = fold32((typename T::U)x);
+    const unsigned b1 = t.first(x32), b2 = t.second(x32);
+    const int nprobe = t.two ? 2 : t.NB;
+    for (int c = 0; c < nprobe; ++c) {
+      const unsigned b = t.two ? (c ? b2 : b1) : ((b1 + (unsigned)c) & (unsigned)(t.NB - 1));
       for (int j = 0; j < kBucketSlots; ++j) {
         K* slotp = t.keys + b * kBucketSlots + j;
         const K k = *reinterpret_cast<volatile K*>(slotp);
@@ -642,10 +657,28 @@ __device__ __forceinline__ void slow_insert(K x, const LocalTable<K>& t, unsigne
 // that a warp's misses at different positions share one pass of the slow
 // path.  Keys equal to the type minimum (the tables' empty marker) are only
 // counted.
+// Direct table of the main path when the sample holds few distinct keys
+// (u <= kDirectMaxKeys): a multiplier that sends every sampled key to its
+// own slot of kDirectSlots is searched for, and a slot holds the key's index
+// in a dense list (kDirectMaxKeys means none; that entry holds the type
+// minimum, which no looked-up key equals).  A lookup is one byte load, one
+// key compare and one counter atomic on a lane-private replica (the bank is
+// the lane); keys outside the sample fall through to the bucket table.
+constexpr int kDirectSlotBits = 14;
+constexpr int kDirectSlots = 1 << kDirectSlotBits;
+constexpr int kDirectMaxKeys = 255;
+constexpr int kDirectBytes = kDirectSlots + 256 * 8 + 256 * 32 * 4;   // index, keys, counters
+
 template <typename K, bool TINY>
 struct KeyCounter {
   using T = KeyTraits<K>;
   LocalTable<K> lt;
+  // direct table (main path; dslot == nullptr: none)
+  const unsigned char* dslot;
+  const K* dkey;
+  unsigned* dcnt;
+  unsigned dmult;
+  int lane;
   // tiny path
   unsigned long long tmult;
   unsigned tvalid;
@@ -667,15 +700,21 @@ struct KeyCounter {
       ++special;
       return true;
     }
-    if (!TINY && lt.keys) {
-      // Slots of a bucket fill in order and a key sits in the first bucket
-      // (from its home on) that had a free slot when it came, so a bucket
-      // whose last slot is still free ends the search.  Up to kFastBuckets
-      // buckets are searched here; the rest (about 1 % of the keys at the
-      // largest load, 1/2) go to the slow path.
+    if (!TINY && dslot) {
+      const unsigned i = dslot[local_bucket_m(fold32((typename T::U)x), dmult, kDirectSlotBits)];
+      if (dkey[i] == x) {
+        atomicAdd(dcnt + i * 32u + (unsigned)lane, 1u);
+        return true;
+      }
+    }
+    if (!TINY && lt.keys && !lt.two) {
+      // Linear probing over buckets (load <= 1/4): a key sits in the first
+      // bucket from its home on that had a free slot when it came, so a
+      // bucket whose last slot is free ends the search; up to kFastBuckets
+      // buckets here, the rest in the slow path.
       constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
       constexpr int kFastBuckets = 3;
-      unsigned b = lt.home(x);
+      unsigned b = lt.first(fold32((typename T::U)x));
       #pragma unroll
       for (int probe = 0; probe < kFastBuckets; ++probe) {
         K k[kBucketSlots];
@@ -690,6 +729,30 @@ struct KeyCounter {
         }
         if (k[kBucketSlots - 1] == T::min_key()) break;
         b = (b + 1) & (unsigned)(lt.NB - 1);
+      }
+      return false;
+    }
+    if (!TINY && lt.keys) {
+      // Two-choice buckets (load up to 1/2): both candidate buckets with two
+      // independent 16-byte loads; a key found in either is counted.
+      constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
+      const unsigned x32 = fold32((typename T::U)x);
+      const unsigned b1 = lt.first(x32), b2 = lt.second(x32);
+      K k1[kBucketSlots], k2[kBucketSlots];
+      load_bucket(lt.keys + b1 * kBucketSlots, k1);
+      load_bucket(lt.keys + b2 * kBucketSlots, k2);
+      int hit = -1;
+      #pragma unroll
+      for (int j = kBucketSlots - 1; j >= 0; --j) {
+        if (k2[j] == x) hit = (int)(b2 * kBucketSlots) + j;
+      }
+      #pragma unroll
+      for (int j = kBucketSlots - 1; j >= 0; --j) {
+        if (k1[j] == x) hit = (int)(b1 * kBucketSlots) + j;
+      }
+      if (hit >= 0) {
+        lt.add((unsigned)hit);
+        return true;
       }
     }
     return false;
@@ -752,10 +815,69 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
   while (R > 1 && S * (kKeyBytes + 4 * R) > budget) R >>= 1;
   const bool use_local = TINY || (k_hat <= (unsigned long long)smax);
 
-  // Shared memory: table (| tiny counters) | misc ... barriers | ring (top).
-  const int table_bytes = TINY ? kTinyTableBytes + kTinyBuckets * kConsumers * 4
-                               : (use_local ? S * (kKeyBytes + 4 * R) : 0);
-  unsigned char* tbase = smem;
+  // Direct table: few sampled keys, all of them in slots of their own.
+  // Its multiplier is searched for first (32 warps, one candidate each per
+  // round, a 16384-bit occupancy bitmap per warp in the table's bytes).
+  const int u_all = (int)r.u;
+  unsigned char* dbase = smem;
+  unsigned* dflag = reinterpret_cast<unsigned*>(smem + kLocalTableBytes);   // [0] multiplier, [1] kmin position
+  int nd = 0;
+  unsigned dmult = 0;
+  if (!TINY && use_local && u_all <= kDirectMaxKeys && k_hat <= (unsigned long long)kDirectMaxKeys) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned* bm = reinterpret_cast<unsigned*>(smem) + w * (kDirectSlots / 32);
+    static_assert(kWarps * (kDirectSlots / 8) <= kLocalTableBytes, "search bitmaps in the table's bytes");
+    if (threadIdx.x == 0) {
+      dflag[0] = 0u;
+      dflag[1] = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < u_all; j += blockDim.x)
+      if ((K)__ldcg(p.sample_keys + j) == kmin) dflag[1] = (unsigned)j;
+    const unsigned base = p.local_mult ? (p.local_mult | 1u) : 0x9E3779B1u;
+    for (int round = 0; round < 4; ++round) {
+      const unsigned m = (base * (2u * (unsigned)(round * kWarps + w) + 1u)) | 1u;
+      for (int i = l; i < kDirectSlots / 32; i += 32) bm[i] = 0u;
+      __syncwarp();
+      bool coll = false;
+      for (int j = l; j < u_all; j += 32) {
+        const K kj = (K)__ldcg(p.sample_keys + j);
+        if (kj == kmin) continue;
+        const unsigned sl = local_bucket_m(fold32((typename T::U)kj), m, kDirectSlotBits);
+        const unsigned bit = 1u << (sl & 31u);
+        coll |= (atomicOr(bm + (sl >> 5), bit) & bit) != 0u;
+      }
+      coll = __any_sync(0xffffffffu, coll);
+      __syncthreads();
+      if (!coll && l == 0) atomicCAS(dflag, 0u, m);   // any collision-free candidate
+      __syncthreads();
+      if (dflag[0] != 0u) break;
+    }
+    dmult = dflag[0];
+    nd = dmult ? u_all - (dflag[1] != 0xFFFFFFFFu ? 1 : 0) : 0;
+    __syncthreads();
+  }
+  const bool dmode = nd > 0;
+  // Two-choice buckets once the table may pass a quarter full.
+  const int two_choice = (!TINY && 4ull * k_hat > (unsigned long long)smax) ? 1 : 0;
+  unsigned char* dslot = dbase;
+  K* dkey = reinterpret_cast<K*>(dbase + kDirectSlots);
+  unsigned* dcnt = reinterpret_cast<unsigned*>(dbase + kDirectSlots + 256 * 8);
+  if (dmode) {
+    // the bucket table behind it: what is left of the budget, for keys
+    // outside the sample
+    S = 256;
+    while (S < 2048 && (unsigned long long)S < 4ull * k_hat) S <<= 1;
+    R = (int)p.replicas_max;
+    while (R > 1 && S * (kKeyBytes + 4 * R) > kLocalTableBytes - kDirectBytes) R >>= 1;
+  }
+  static_assert(kDirectBytes + 2048 * (8 + 4) <= kLocalTableBytes, "direct table and bucket table");
+
+  // Shared memory: [direct table] table (| tiny counters) | misc ... barriers | ring (top).
+  unsigned char* tbase = smem + (dmode ? kDirectBytes : 0);
+  const int table_bytes = (dmode ? kDirectBytes : 0) +
+                          (TINY ? kTinyTableBytes + kTinyBuckets * kConsumers * 4
+                                : (use_local ? S * (kKeyBytes + 4 * R) : 0));
   K* lkeys = reinterpret_cast<K*>(tbase);
   unsigned* lcnt = reinterpret_cast<unsigned*>(tbase + (size_t)S * kKeyBytes);
   unsigned* tcnt = reinterpret_cast<unsigned*>(tbase + kTinyTableBytes);           // kTinyBuckets x kConsumers
@@ -789,8 +911,24 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     }
   }
   if (threadIdx.x == 0) *local_occ = 0u;
+  if (dmode) {
+    for (int i = threadIdx.x; i < kDirectSlots; i += blockDim.x) dslot[i] = (unsigned char)kDirectMaxKeys;
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) dcnt[i] = 0u;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) dkey[i] = kmin;
+  }
   __syncthreads();
-  if (!TINY && use_local) {
+  if (dmode) {
+    const unsigned kpos = dflag[1];
+    for (int j = threadIdx.x; j < u_all; j += blockDim.x) {
+      if ((unsigned)j == kpos) continue;
+      const K kj = (K)__ldcg(p.sample_keys + j);
+      const int i = j - ((unsigned)j > kpos && kpos != 0xFFFFFFFFu ? 1 : 0);
+      dkey[i] = kj;
+      dslot[local_bucket_m(fold32((typename T::U)kj), dmult, kDirectSlotBits)] = (unsigned char)i;
+    }
+  }
+  __syncthreads();
+  if (!TINY && use_local && !dmode) {
     // Seed with the distinct sampled keys (counts 0), so that the frequent
     // keys are found in their buckets from the first chunk on.
     LocalTable<K> seed;
@@ -803,6 +941,7 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     seed.R = R;
     seed.lane_rep = 0;
     seed.mult = p.local_mult ? (p.local_mult | 1u) : 0x9E3779B1u;
+    seed.two = two_choice;
     seed.gt = global_table(p);
     const int u = (int)r.u;
     for (int j = threadIdx.x; j < u; j += blockDim.x) {
@@ -823,6 +962,7 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     lt.R = R;
     lt.lane_rep = (threadIdx.x & 31) & (R - 1);
     lt.mult = p.local_mult ? (p.local_mult | 1u) : 0x9E3779B1u;
+    lt.two = two_choice;
     lt.gt = global_table(p);
     lt.gt.stop = ring.skip_flag;
     if (tiny_hash) {
@@ -833,6 +973,7 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
       kc.tkey = tkey;
       kc.tcnt = tcnt + (threadIdx.x < kConsumers ? threadIdx.x : 0);
       kc.special = 0;
+      kc.dslot = nullptr;
       const bool res = ring.run(p, keys, &c->overflow, kc, sc);
       // Tiny buckets: add up the per-thread counters, insert each sampled key.
       for (int j = 0; j < nt; ++j) {
@@ -851,10 +992,28 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
     KeyCounter<K, false> kc;
     kc.lt = lt;
     kc.special = 0;
+    kc.dslot = dmode ? dslot : nullptr;
+    kc.dkey = dkey;
+    kc.dcnt = dcnt;
+    kc.dmult = dmult;
+    kc.lane = threadIdx.x & 31;
     const bool res = ring.run(p, keys, &c->overflow, kc, sc);
     special_out(c, kc.special, red);
     return res;
   }();
+
+  if (dmode) {
+    GlobalTable g = global_table(p);
+    g.stop = ring.skip_flag;
+    const int rot = (int)((sc.part() * 37u) % (unsigned)nd);
+    for (int i0 = threadIdx.x; i0 < nd; i0 += blockDim.x) {
+      const int i = (i0 + rot) % nd;
+      unsigned tot = 0;
+      #pragma unroll 8
+      for (int q = 0; q < 32; ++q) tot += dcnt[i * 32 + ((q + i) & 31)];
+      if (tot) global_insert(g, (unsigned long long)(long long)dkey[i], tot);
+    }
+  }
 
   // Flush the shared table into the global table.  CTAs hold mostly the
   // same keys in the same local slots; each starts at its own offset so
@@ -1783,6 +1942,15 @@ __device__ void phase_emit(const Params& p, unsigned long long npairs, unsigned 
 // ---------------------------------------------------------------------------
 // The persistent pipeline kernel (N >= 2048).
 // ---------------------------------------------------------------------------
+// CTA 0 zeroes the control block of the next launch on this workspace (two
+// blocks alternate, so no separate zeroing step runs between launches).
+__device__ __forceinline__ void zero_next_ctrl(const Params& p) {
+  if (blockIdx.x != 0 || !p.ctrl_next) return;
+  static_assert(sizeof(Ctrl) % 8 == 0, "control block in 8-byte words");
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(p.ctrl_next);
+  for (int i = threadIdx.x; i < (int)(sizeof(Ctrl) / 8); i += blockDim.x) w[i] = 0ull;
+}
+
 template <class S>
 __device__ __forceinline__ void mark(Ctrl* c, int i, const S& sc) {
   if (sc.lead()) c->rec.timeline[i] = global_timer_ns();

@@ -13,6 +13,7 @@ template <typename K>
 __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
   extern __shared__ __align__(128) unsigned char smem[];
   const GridScope sc;
+  zero_next_ctrl(p);
   mark(p.ctrl, 0, sc);
   if (!((p.test_flags & kTestSkipBarrier) && blockIdx.x == 0)) {  // test: CTA 0 never arrives
     unsigned epoch = 0;
@@ -28,6 +29,7 @@ __global__ void __launch_bounds__(kThreads, 1) pipeline_kernel(Params p) {
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 1) small_kernel(Params p) {
   extern __shared__ __align__(128) unsigned char smem[];
+  zero_next_ctrl(p);
   small_body<K>(p, smem);
 }
 
