@@ -707,7 +707,7 @@ struct KeyCounter {
         return true;
       }
     }
-    if (!TINY && lt.keys && !lt.two) {
+    if (!TINY && !lt.two) {
       // Linear probing over buckets (load <= 1/4): a key sits in the first
       // bucket from its home on that had a free slot when it came, so a
       // bucket whose last slot is free ends the search; up to kFastBuckets
@@ -732,7 +732,7 @@ struct KeyCounter {
       }
       return false;
     }
-    if (!TINY && lt.keys) {
+    if (!TINY) {
       // Two-choice buckets (load up to 1/2): both candidate buckets with two
       // independent 16-byte loads; a key found in either is counted.
       constexpr int kBucketSlots = LocalTable<K>::kBucketSlots;
@@ -783,6 +783,38 @@ struct KeyCounter {
       const int i = __ffs(miss) - 1;
       miss &= miss - 1;
       slow_insert<K>(reinterpret_cast<const K*>(src + (i / VPE) * STRIDE)[i % VPE], lt, 1u);
+    }
+  }
+};
+
+// Count phase without a shared table (K_hat above what one CTA's table
+// holds; Sec. 4.5's L2-level table): every key is inserted into the global
+// Eq. 4 table.  A functor of its own, so that the shared-table counter's
+// loop never has to allow for a missing table (measured: 8-12 us less per
+// 3e7-key count for K <= 1000).  Streaming the share with plain loads and
+// several probes in flight per thread measured slower than this (about 1 ms
+// against 0.62-0.71 ms for K = 1e4..1.3e5).
+template <typename K>
+struct GlobalCounter {
+  using T = KeyTraits<K>;
+  GlobalTable g;
+  unsigned long long special;
+
+  __device__ __forceinline__ void single(K x) {
+    if (x == T::min_key()) ++special;
+    else global_insert(g, (unsigned long long)(long long)x, 1u);
+  }
+  template <int NV, int STRIDE>
+  __device__ __forceinline__ void chunk(const typename T::Vec* src, unsigned cnt) {
+    constexpr int VPE = T::kVec;
+    #pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if ((unsigned)i < cnt) {
+        K e[VPE];
+        unpack(src[i * STRIDE], e);
+        #pragma unroll
+        for (int q = 0; q < VPE; ++q) single(e[q]);
+      }
     }
   }
 };
@@ -987,6 +1019,14 @@ __device__ bool phase_count(const Params& p, const K* keys, unsigned char* smem,
         }
       }
       special_out(c, kc.special, red);
+      return res;
+    }
+    if (!use_local) {
+      GlobalCounter<K> gc;
+      gc.g = lt.gt;
+      gc.special = 0;
+      const bool res = ring.run(p, keys, &c->overflow, gc, sc);
+      special_out(c, gc.special, red);
       return res;
     }
     KeyCounter<K, false> kc;

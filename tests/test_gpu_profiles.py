@@ -52,3 +52,17 @@ def test_grouped(dtype, k):
 def test_almost_sorted(dtype, k, swaps):
     check(G.almost_sorted(300_000, k, swaps, dtype, seed=k), argsort=(k == 200))
     check(G.almost_sorted(300_000, k, 0, dtype, seed=k))   # sorted: the bypass
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("k", [3, 50, 1500, 4000, 30_000])
+@pytest.mark.parametrize("mean_run", [2.0, 9.0, 300.0])
+def test_runs_in_every_table_form(k, mean_run, dtype):
+    # Runs of equal keys are counted once per run with the run's length (the
+    # run-length case of Sec. 4.4); K from the tiny path (3) through the
+    # direct table (50), linear probing (1500), two-choice buckets (4000) to
+    # the global table (30000), runs short and long, crossing vector, warp
+    # and chunk boundaries.
+    x = G.runs_column(700_001, k, mean_run, "uniform", dtype, seed=k + int(mean_run))
+    check(x)
+    check(x[::-1].copy())
