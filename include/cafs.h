@@ -180,18 +180,22 @@ cafs_status cafs_sort_host(const void* host_keys, size_t n, cafs_dtype dtype,
                            void* host_out, cafs_report* report, void* stream);
 
 /* Allocation-free variant of cafs_sort (the paper has no counterpart).  For
- * callers that cannot allocate device memory -- code inside a CUDA graph
- * capture that must not add allocation nodes, engines that allow no memory
- * outside pre-reserved pools, locked-down allocators: this call performs no
- * cudaMalloc/cudaFree and calls no allocating library routine.  Its scratch
- * is one file-scope device array of about 24 MiB that every GPU loading the
- * library holds until the process exits.  n must be <= 2^19 (524288) keys,
- * else CAFS_ERR_TOO_LARGE; other arguments as for cafs_sort.  The first call
- * on a device resolves the array's device address and sets kernel
- * attributes, so make that first call before any stream capture.  All calls
- * share the array (it keeps the previous call's contents and is re-cleared
- * per call): calls whose work overlaps on the GPU -- other streams, other
- * host threads -- race and must be serialised by the caller.  No report. */
+ * callers that cannot allocate device memory: engines that hand out only
+ * pre-reserved memory pools and forbid any other allocation, processes that
+ * run under a fixed device-memory budget, and latency-critical loops where
+ * the implicit device synchronisation of cudaMalloc/cudaFree is not
+ * acceptable.  This call performs no cudaMalloc/cudaFree and calls no
+ * allocating library routine.  Its scratch is one file-scope device array of
+ * about 25 MiB that every GPU loading the library holds until the process
+ * exits.  n must be <= 2^19 (524288) keys, else CAFS_ERR_TOO_LARGE; other
+ * arguments as for cafs_sort.  The first call on a device resolves the
+ * array's device address and sets kernel attributes, so make that first call
+ * before any stream capture.  All calls share the array (it keeps the
+ * previous call's contents; the control block and the hash table's used
+ * slots are cleared by every call): calls whose work overlaps on the GPU --
+ * other streams, other host threads -- race and must be serialised by the
+ * caller.  No report: a device-side failure (a bounded wait that ran out)
+ * is not reported by this call, and the output is then undefined. */
 cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype dtype, void* out,
                               void* stream);
 

@@ -5,9 +5,12 @@ The knobs never change a result (tests check that); they trade speed:
 emit_tile_vec / 1024), ``local_slots_max`` and ``replicas_max`` size the
 per-CTA shared hash table (its capacity and counter replicas),
 ``grid_min_n`` / ``defer_min_n`` / ``cta_table_slots`` decide which columns
-the whole grid sorts, and ``ctas`` is the number of CTAs of the launch.  The
-threads per CTA are fixed at 1024 by the kernel's shared-memory layout (one
-226 KB CTA per SM).
+the whole grid sorts, and ``ctas`` is the number of CTAs of the launch.  Two
+choices are not run-time knobs and so are not searched: the threads per CTA
+(1024) and the split of the 226 KB of shared memory between the bulk-copy
+ring (124 KB) and the count tables are compile-time constants of the kernel
+(one CTA per SM; 512-thread CTAs and smaller rings measured slower for the
+count phase).
 
 Search: coordinate descent from the defaults -- one knob at a time over its
 candidate values, keeping the fastest, two rounds.  Every measurement is a
@@ -30,6 +33,8 @@ SPACE = {
     "replicas_max": [8, 16, 32],
     "grid_min_n": [0, 1 << 19, 1 << 20, 1 << 21, 1 << 22],
     "defer_min_n": [0, 1 << 16, 1 << 18, 1 << 20],
+    "cta_table_slots": [0, 1 << 14, 1 << 16, 1 << 18],
+    "ctas": [0, 114, 76],
 }
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "cafs_gb300", "autotune.json")

@@ -1,16 +1,16 @@
 // cafs_sort_noalloc: the same sort for callers that must not allocate device
 // memory, with every byte of scratch in one file-scope device array.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph capture that is not allowed to add memory nodes, engines that hand
-// out only pre-reserved pools and forbid any other allocation, or processes
-// whose allocator is locked down for determinism.  For them this entry point
-// takes its scratch (control block, hash table, pair arrays, radix buffers)
-// from `g_noalloc_scratch`, a static __device__ array that every GPU loading
-// the library holds until the process exits.  Columns are limited to
-// kNoAllocMaxKeys keys.  Calls share the array, so calls whose work overlaps
-// on the GPU (different streams, different host threads) race with each
-// other and must be serialised by the caller.
+// Some callers cannot call cudaMalloc at all: engines that hand out only
+// pre-reserved pools and forbid any other allocation, processes held to a
+// fixed device-memory budget, and latency-critical loops that cannot afford
+// the implicit device synchronisation of cudaMalloc/cudaFree.  For them this
+// entry point takes its scratch (control block, hash table, pair arrays,
+// radix buffers) from `g_noalloc_scratch`, a static __device__ array that
+// every GPU loading the library holds until the process exits.  Columns are
+// limited to kNoAllocMaxKeys keys.  Calls share the array, so calls whose
+// work overlaps on the GPU (different streams, different host threads) race
+// with each other and must be serialised by the caller.
 
 #include <cstdint>
 #include <cstring>
@@ -144,17 +144,21 @@ extern "C" cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype 
   p.local_slots_max = kLocalSlotsMax;
   p.replicas_max = kDefaultReplicasMax;
   p.emit_tile_vec = kEmitTileVecDefault;
-  p.timeout_ns = 1000000000ull;
+  p.timeout_ns = wait_timeout_ns();
   next_hash_multipliers(&p.hash_mult, &p.local_mult);
 
   // The array keeps the previous call's contents: the control block must
   // start at zero and the hash table empty (every key slot the empty marker,
-  // every count zero).  Look-back words are tagged with the call generation
-  // and need no clearing.
+  // every count zero).  The rest of the scratch needs no clearing: every
+  // radix pass writes each CTA's digit counts and bases (and the pair bucket
+  // sort its per-CTA counts) before any CTA reads them, with a grid barrier
+  // in between, and the pair and temp arrays are written before they are
+  // read within a call.
   if (cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return CAFS_ERR_CUDA;
   if (n >= kSmallN) {
     const unsigned long long tcap = table_capacity(n, dtype);
     if (launch_fill_u64(p.tkeys, tcap, 0x8000000000000000ull, s) != cudaSuccess) return CAFS_ERR_CUDA;
+    count_launches(1);
     if (cudaMemsetAsync(p.tcounts, 0, tcap * 4, s) != cudaSuccess) return CAFS_ERR_CUDA;
   }
   cudaError_t e;
@@ -166,5 +170,7 @@ extern "C" cafs_status cafs_sort_noalloc(const void* keys, size_t n, cafs_dtype 
     if (grid < 1) grid = 1;
     e = launch_pipeline(p, dtype, (int)grid, s);
   }
-  return e == cudaSuccess ? CAFS_OK : CAFS_ERR_CUDA;
+  if (e != cudaSuccess) return CAFS_ERR_CUDA;
+  count_launches(1);
+  return CAFS_OK;
 }

@@ -2,31 +2,35 @@
 // shared by the single-column kernels and the batched kernel.
 //
 // For one column of N >= 2048 keys the CTAs of a scope (the whole cooperative
-// grid, or one CTA) run the pipeline of Sec. 4.1 for
-// a column of N >= 2048 keys; phases are separated by a bounded grid barrier:
+// grid, or one CTA) run the pipeline of Sec. 4.1; phases are separated by a
+// bounded grid barrier:
 //
-//   0  sampler + Chao1 + dispatcher record          (Alg. 2, Eq. 5, Eq. 6,
-//                                                    Alg. 3; CTA 0)
+//   0  sampler + Chao1 + dispatcher record (Alg. 2, Eq. 5, Eq. 6, Alg. 3):
+//      the CTAs gather the 1024 strided samples together, then every CTA
+//      computes the same estimate and dispatch decision itself
 //   1  IsMonotone full scan, only when the 1024 samples ascend (Alg. 3);
 //      a sorted column is copied through (bypass)
 //   2  count: every CTA streams its share of the column through a shared
 //      memory ring filled by bulk copies (cp.async.bulk + mbarrier) and counts
-//      it, either against the <= 8 sampled keys in registers (tiny path,
-//      Sec. 4.4) or in a per-CTA open-addressing table (main path, Sec. 4.2)
-//      that is merged into a global table hashed with Eq. 4; the global table
-//      counts distinct keys and raises the overflow guard when they exceed
-//      L = C/2 (Eq. 6, Alg. 4)
+//      it against the <= 8 sampled keys (tiny path, Sec. 4.4) or in a per-CTA
+//      table (main path, Sec. 4.2: a direct table of the sampled keys, linear
+//      probing over 16-byte buckets, or two-choice buckets) that is merged
+//      into a global table hashed with Eq. 4; above what a CTA's table holds,
+//      every key goes to the global table.  The global table counts distinct
+//      keys and raises the overflow guard when they exceed L = C/2 (Eq. 6,
+//      Alg. 4)
 //   3  the K' (key, count) pairs are put in key order and their counts
 //      exclusive-scanned (Alg. 4): for K' <= 4096 every CTA computes, for its
 //      share of the pairs, the rank and the run offset directly (number of
-//      smaller keys and the sum of their counts); larger K' go through an LSD
-//      radix sort followed by a two-level scan
+//      smaller keys and the sum of their counts); larger K' go through a
+//      splitter bucket sort (one key range per CTA, sorted in shared memory)
 //   4  emit: every output tile looks up its runs and writes them with 16-byte
 //      streaming stores (the paper's fill_n per pair)
 //   R  radix fallback (the paper's pdqsort: 2*K_hat > N, or the guard fired):
-//      LSD radix sort, 8-bit digits; one histogram read for all passes, then
-//      per pass a reduce-then-scan over per-CTA digit counts and an in-order
-//      stable scatter; passes whose digit is constant are skipped.
+//      LSD radix sort, 8-bit digits; per pass a reduce-then-scan over per-CTA
+//      digit counts (pass 0's count read also finds the key bits that vary,
+//      so passes whose digit is constant are skipped) and an in-order stable
+//      scatter.
 //
 // Columns with N < 2048 are sorted by a single CTA in shared memory
 // (Table 2: "sampling does not amortize").
