@@ -486,7 +486,8 @@ struct GlobalTable {
   unsigned* counts;
   unsigned* claimed;
   Ctrl* ctrl;
-  unsigned long long C, L;
+  unsigned long long C;     // Eq. 6's slots
+  unsigned long long cap;   // slots the workspace's table holds (>= C)
   int logC;
   unsigned long long mult;   // Eq. 4 multiplier (odd)
   // The CTA's shared copy of the guard (null: none).  Once the guard has
@@ -503,18 +504,44 @@ __device__ __forceinline__ GlobalTable global_table(const Params& p) {
   g.claimed = p.claimed;
   g.ctrl = p.ctrl;
   g.C = p.ctrl->rec.C;
-  g.L = p.ctrl->rec.L;
+  g.cap = p.table_cap;
   g.logC = log2_pow2(g.C);
   g.mult = p.hash_mult ? (p.hash_mult | 1ull) : kPhi;
   g.stop = nullptr;
   return g;
 }
 
+// Slots of the global table in use.  Tables of Eq. 6 up to kSlackMaxC slots
+// belong to columns counted in shared tables (K_hat within one CTA's table,
+// whose C is at most 65536 slots for either key width); they use up to
+// kGuardSlack times C slots, within the workspace's table, and the count goes
+// on until half of those are claimed.  Alg. 4's guard (distinct keys >
+// L = C/2) still decides the branch, but when the count completes below the
+// larger limit its counts are emitted instead of running the radix fallback
+// on the whole column (Chao1 underestimates K on skewed data by a few times:
+// the Zipf(1.1) columns of K = 1e4 .. 1.3e5 at N = 3e7 hold 1.2 to 7.9 times
+// L distinct keys).  Such a global table only holds the keys the shared
+// tables flush or spill, so its size does not slow the count.  Larger Eq. 6
+// tables belong to columns counted in the global table alone, where the
+// table is the hot structure and keeps its Eq. 6 size.  Every insert of a
+// call computes the same size from the same (C, cap).
+constexpr unsigned long long kGuardSlack = 8;
+constexpr unsigned long long kSlackMaxC = 65536;
+
+__device__ __forceinline__ int table_log2(unsigned long long C, unsigned long long cap, int logC) {
+  if (C > kSlackMaxC) return logC;
+  const unsigned long long big = C * kGuardSlack;
+  return log2_pow2(big < cap ? big : (cap > C ? cap : C));
+}
+
 static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long long key64, unsigned inc) {
   Ctrl* c = g.ctrl;
-  const unsigned long long mask = g.C - 1;
-  const unsigned long long h = hash_slot_m(key64, g.mult, g.logC);
-  for (unsigned long long probe = 0; probe < g.C; ++probe) {
+  const int lg = table_log2(g.C, g.cap, g.logC);
+  const unsigned long long size = 1ull << lg;
+  const unsigned long long limit = size / 2;
+  const unsigned long long mask = size - 1;
+  const unsigned long long h = hash_slot_m(key64, g.mult, lg);
+  for (unsigned long long probe = 0; probe < size; ++probe) {
     // Once the guard has fired the counts are discarded: stop probing.
     if (g.stop && *reinterpret_cast<volatile unsigned*>(g.stop)) return;
     if ((probe & 3ull) == 3ull && ld_relaxed_u32(&c->overflow)) {
@@ -531,9 +558,9 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
       const unsigned long long old = atomicCAS(g.keys + slot, kEmpty64, key64);
       if (old == kEmpty64) {
         const unsigned idx = atomicAdd(&c->occupancy, 1u);
-        if (idx < g.C) g.claimed[idx] = (unsigned)slot;
+        if (idx < size) g.claimed[idx] = (unsigned)slot;
         atomicAdd(g.counts + slot, inc);
-        if (idx >= g.L) {
+        if (idx >= limit) {
           atomicExch(&c->overflow, 1u);
           if (g.stop) *reinterpret_cast<volatile unsigned*>(g.stop) = 1u;
         }
@@ -2081,7 +2108,11 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
   const unsigned occ = (unsigned)cnt_smem[0];
   const unsigned long long special = cnt_smem[1];
   const unsigned long long kp = (unsigned long long)occ + (special ? 1ull : 0ull);
-  const bool overflow = cnt_smem[2] != 0ull || kp > r.L;
+  // Alg. 4's guard (distinct keys > L) decides the branch; the count itself
+  // stops only past the global table's own limit (see table_log2), and only
+  // then is the column left to the radix fallback.
+  const bool stopped = cnt_smem[2] != 0ull;
+  const bool overflow = stopped || kp > r.L;
   __syncthreads();
   // Sec. 4.4: the tiny counters add up to N exactly when every key is one
   // of the u sampled keys, i.e. when the column has exactly u distinct keys.
@@ -2091,10 +2122,10 @@ __device__ int column_body(const Params& p, unsigned char* smem, const S& sc, un
   if (sc.lead()) {
     r.path = path;
     r.k_distinct = overflow ? 0ull : kp;
-    r.n_pairs = overflow ? 0ull : kp;
+    r.n_pairs = stopped ? 0ull : kp;
   }
-  if (overflow) {
-    // Guard fired: clear the claimed slots; the caller runs the radix sort.
+  if (stopped) {
+    // The count stopped: clear the claimed slots; the caller runs the radix sort.
     reset_claimed(p, occ, sc);
     return kColumnRadix;
   }

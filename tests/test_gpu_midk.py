@@ -1,14 +1,14 @@
-"""Parity of the mid-K paths (K_hat above one CTA's shared table) with the
-CPU oracle, through the C ABI.
+"""Parity of the mid-K paths with the CPU oracle, through the C ABI.
 
-Columns whose estimate exceeds the per-CTA table are counted by owner CTAs
-(every key sent to the CTA that owns it, then counted there in shared
-memory), and pair sets larger than the rank pass are ordered by a splitter
-bucket sort.  Neither may change a result, the estimate, the branch or K'
+Columns whose estimate exceeds one CTA's shared table are counted in the
+global Eq. 4 table, pair sets larger than the rank pass are ordered by a
+splitter bucket sort, and columns whose estimate was too low (the guard's
+overflow branch) are still emitted from their counts when the count
+completed.  None of this may change a result, the estimate, the branch or K'
 (Sec. 4.2, Alg. 3, Alg. 4).  The cases span ragged lengths, both key widths,
-uniform and Zipf frequencies, the type minimum, keys built so that every one
-of them has the same owner (the region and owner-table overflow fallbacks),
-per-call hash seeds and the stable argsort on the same columns.
+uniform and Zipf frequencies, the type minimum, keys that all share the high
+bits of one multiplicative hash, per-call hash seeds and the stable argsort
+on the same columns.
 """
 
 import numpy as np
@@ -95,8 +95,8 @@ def owner_colliding_keys(count: int, dtype, seed: int) -> np.ndarray:
 
 @pytest.mark.parametrize("dtype", [np.int32, np.int64])
 def test_all_keys_one_owner(dtype):
-    # Every key belongs to owner 0: its regions overflow (keys go straight to
-    # the global table) and its shared table fills (the rest go there too).
+    # Every key shares the high 32 bits of one multiplicative hash: the
+    # counts must not depend on where such keys land.
     vals = owner_colliding_keys(20_000, dtype, seed=5)
     rng = np.random.default_rng(6)
     x = vals[rng.integers(0, vals.size, size=2_000_000)]
@@ -141,7 +141,7 @@ def test_mid_k_argsort(dtype):
 
 
 def test_mid_k_repeated_and_interleaved():
-    # the global table and the partition regions are reused call after call
+    # the global table and the pair arrays are reused call after call
     seq = [G.column(1_000_000, 50_000, "uniform", np.int64, 1),
            G.column(1_000_000, 200, "uniform", np.int64, 2),
            G.spill_trigger(1_000_000, np.int64, 3),
