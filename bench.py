@@ -468,6 +468,10 @@ def bench_served(torch, cafs, rates=(1e3, 1e4, 1e5), budget=8 << 30, pool_size=2
                                                    "K log-uniform [2, 1e5], Zipf 1.1 (pinned host buffers)",
            "latency": "arrival (scheduled) to sorted keys in host memory", "rates": []}
     try:
+        # untimed warm-up: every pool column once, so that the server's arena,
+        # workspaces and plans exist before the first measured trace
+        srv.run_trace(pool, np.arange(pool_size) * 1e-4)
+        cafs.serial_run_trace(pool, np.arange(pool_size) * 1e-4)
         for rate in rates:
             nreq = int(min(20000, max(2000, rate)))
             gaps = G.exponential_gaps(rate, nreq, seed=int(rate))
