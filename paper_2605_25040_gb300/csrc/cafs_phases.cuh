@@ -557,11 +557,18 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
     if (k == kEmpty64) {
       const unsigned long long old = atomicCAS(g.keys + slot, kEmpty64, key64);
       if (old == kEmpty64) {
-        const unsigned idx = atomicAdd(&c->occupancy, 1u);
+        // The lanes of the warp that claim a slot together take their
+        // occupancy indices with one atomic: every claim of every CTA goes
+        // to this one counter, whose atomics the L2 serialises.
+        const unsigned grp = __activemask();
+        const int lead = __ffs(grp) - 1;
+        unsigned first = 0;
+        if ((int)(threadIdx.x & 31u) == lead) first = atomicAdd(&c->occupancy, (unsigned)__popc(grp));
+        const unsigned idx = __shfl_sync(grp, first, lead) + (unsigned)__popc(grp & lanemask_lt());
         if (idx < size) g.claimed[idx] = (unsigned)slot;
         atomicAdd(g.counts + slot, inc);
         if (idx >= limit) {
-          atomicExch(&c->overflow, 1u);
+          if (!ld_relaxed_u32(&c->overflow)) atomicExch(&c->overflow, 1u);
           if (g.stop) *reinterpret_cast<volatile unsigned*>(g.stop) = 1u;
         }
         return;
