@@ -1217,20 +1217,21 @@ __device__ __forceinline__ void half_sync(int h) {
 }
 
 // Lanes of the warp whose digit equals this lane's (digits < 2^9: the
-// radix digit, or 256 for no item), from one ballot per digit bit.  A
-// warp-wide match costs more the more distinct values the warp holds; the
-// ballots cost the same for any mix, which wins on the well-mixed digits of
-// high-entropy passes.  `all_valid`: every lane holds an item (digit < 256).
-__device__ __forceinline__ unsigned digit_peers_ballot(unsigned d, bool all_valid) {
-  unsigned peers = 0xffffffffu;
+// radix digit, or 256 for no item).  The top digit bits go to one match
+// instruction and each low bit to a ballot: ballots and the bit tests around
+// them are ALU work, whose pipe a pass of ballots alone keeps busy, while
+// the match runs in another unit and costs more the more distinct values the
+// warp holds (at most 8 here: 256 >> 5 = 8 tells missing items apart).  On
+// 3e7 distinct int64 keys the whole sort took 2.32 ms with eight ballots,
+// 2.10 ms with a match of 3 bits and 5 ballots, 2.13 ms with 4 + 4, 2.40 ms
+// with 5 + 3, 2.89 ms with a match of each nibble and about 3 ms with one
+// match of the whole digit.
+__device__ __forceinline__ unsigned digit_peers_ballot(unsigned d) {
+  constexpr int kLowBits = 5;
+  unsigned peers = __match_any_sync(0xffffffffu, d >> kLowBits);
   #pragma unroll
-  for (int bit = 0; bit < kRadixBits; ++bit) {
+  for (int bit = 0; bit < kLowBits; ++bit) {
     const unsigned on = (d >> bit) & 1u;
-    const unsigned b = __ballot_sync(0xffffffffu, on);
-    peers &= on ? b : ~b;
-  }
-  if (!all_valid) {
-    const unsigned on = (d >> kRadixBits) & 1u;
     const unsigned b = __ballot_sync(0xffffffffu, on);
     peers &= on ? b : ~b;
   }
@@ -1242,12 +1243,11 @@ __device__ __forceinline__ unsigned digit_peers_ballot(unsigned d, bool all_vali
 // the warp's digit-counter row (zero on entry, the warp's digit counts on
 // exit).
 template <bool kMatch>
-__device__ __forceinline__ void rank_warp_items(unsigned (&rd)[kRadixItems], unsigned short* row,
-                                                int lane, bool all_valid) {
+__device__ __forceinline__ void rank_warp_items(unsigned (&rd)[kRadixItems], unsigned short* row, int lane) {
   #pragma unroll
   for (int j = 0; j < kRadixItems; ++j) {
     const unsigned d = rd[j];
-    const unsigned peers = kMatch ? __match_any_sync(0xffffffffu, d) : digit_peers_ballot(d, all_valid);
+    const unsigned peers = kMatch ? __match_any_sync(0xffffffffu, d) : digit_peers_ballot(d);
     const int leader = __ffs(peers) - 1;
     unsigned old = 0;
     if (lane == leader && d < (unsigned)kRadixDigits) {
@@ -1295,6 +1295,7 @@ struct HalfSmem {
   unsigned base[kRadixDigits];      // digit destination minus its first stage slot
   unsigned scratch[kHalfWarps];
   unsigned scan_part[kHalfThreads];
+  unsigned stop;                    // the half leaves the pass (written before a barrier, read after it)
 };
 
 struct PassSmem {
@@ -1455,11 +1456,10 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     // distinct digits per warp, where the match instruction is cheaper than
     // the ballots: the warp picks one by how many lanes share the digit of
     // the next lane (item 0).
-    const bool full_tile = cnt == (unsigned)kHalfTile;
     const unsigned next_d = __shfl_down_sync(0xffffffffu, rd[0], 1);
     const bool runs = __popc(__ballot_sync(0xffffffffu, lane == 31 || next_d == rd[0])) >= 16;
-    if (runs) rank_warp_items<true>(rd, hs->wcnt + w * kRadixDigits, lane, full_tile);
-    else rank_warp_items<false>(rd, hs->wcnt + w * kRadixDigits, lane, full_tile);
+    if (runs) rank_warp_items<true>(rd, hs->wcnt + w * kRadixDigits, lane);
+    else rank_warp_items<false>(rd, hs->wcnt + w * kRadixDigits, lane);
     half_sync(h);
     // Per digit: exclusive scan over the half's warps and the half-tile total.
     {
@@ -1509,9 +1509,12 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
         }
       }
       __threadfence_block();
+      // One read of the shared failure flag for the whole half: the other
+      // half may raise it while this half's threads read it.
+      hs->stop = *reinterpret_cast<volatile unsigned*>(&ps->failed);
     }
     half_sync(h);
-    if (*reinterpret_cast<volatile unsigned*>(&ps->failed)) break;
+    if (hs->stop) break;
     if (t < kRadixDigits) {
       hs->base[t] = running[t] - hs->tile_start[t];   // destination of stage slot i = base[d] + i
       running[t] += hs->tile_cnt[t];
