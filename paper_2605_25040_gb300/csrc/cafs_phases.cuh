@@ -832,26 +832,74 @@ struct KeyCounter {
 // 3e7-key count for K <= 1000).  Streaming the share with plain loads and
 // several probes in flight per thread measured slower than this (about 1 ms
 // against 0.62-0.71 ms for K = 1e4..1.3e5).
+//
+// Runs of equal keys (Sec. 4.4's run-length case: grouped input, the output
+// of a group-by) are folded before the insert: the lanes of a warp hold
+// 32 * VPE consecutive keys, and when any key in that window equals the one
+// before it, each run in the window is inserted once with its length, so the
+// inserts fall from one per key towards one per run.  A window without such
+// a pair (the usual case off grouped input) costs one shuffle and one vote.
+// The shared-table counter has no such step: every form of it measured
+// slowed its loop by 10-20 % through register pressure.
 template <typename K>
 struct GlobalCounter {
   using T = KeyTraits<K>;
   GlobalTable g;
   unsigned long long special;
 
-  __device__ __forceinline__ void single(K x) {
-    if (x == T::min_key()) ++special;
-    else global_insert(g, (unsigned long long)(long long)x, 1u);
+  __device__ __forceinline__ void insert(K x, unsigned inc) {
+    if (x == T::min_key()) special += inc;
+    else global_insert(g, (unsigned long long)(long long)x, inc);
   }
+  __device__ __forceinline__ void single(K x) { insert(x, 1u); }
+
+  // The vectors src[0], src[STRIDE], ... (cnt <= NV of them, fewer only in
+  // the higher lanes at the end of a chunk); lane l's vector i follows lane
+  // l - 1's in the column.
   template <int NV, int STRIDE>
   __device__ __forceinline__ void chunk(const typename T::Vec* src, unsigned cnt) {
     constexpr int VPE = T::kVec;
+    constexpr unsigned kAll = (1u << VPE) - 1u;
+    const unsigned lane = threadIdx.x & 31u;
     #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      if ((unsigned)i < cnt) {
-        K e[VPE];
+      const bool have = (unsigned)i < cnt;
+      K e[VPE];
+      if (have) {
         unpack(src[i * STRIDE], e);
+      } else {
         #pragma unroll
-        for (int q = 0; q < VPE; ++q) single(e[q]);
+        for (int q = 0; q < VPE; ++q) e[q] = (K)0;
+      }
+      // hm bit q: the key at position q of this lane starts a run (a lane
+      // without a vector counts as a run start: it ends the window).
+      const K prev = __shfl_up_sync(0xffffffffu, e[VPE - 1], 1);
+      unsigned hm = (lane == 0u || prev != e[0]) ? 1u : 0u;
+      #pragma unroll
+      for (int q = 1; q < VPE; ++q) hm |= (e[q] != e[q - 1]) ? (1u << q) : 0u;
+      if (!have) hm = 1u;
+      if (__all_sync(0xffffffffu, hm == kAll || !have)) {
+        if (have) {
+          #pragma unroll
+          for (int q = 0; q < VPE; ++q) insert(e[q], 1u);
+        }
+        continue;
+      }
+      // Window position of the first run start after this lane's keys.
+      const unsigned starts = __ballot_sync(0xffffffffu, hm != 0u);
+      const unsigned later = starts & ~((2u << lane) - 1u);
+      const int nl = later ? __ffs(later) - 1 : 32;
+      const int nfirst = __shfl_sync(0xffffffffu, __ffs(hm) - 1, nl & 31);
+      const unsigned after = nl < 32 ? (unsigned)(nl * VPE + nfirst) : 32u * VPE;
+      if (have) {
+        #pragma unroll
+        for (int q = 0; q < VPE; ++q) {
+          if ((hm >> q) & 1u) {
+            const unsigned rest = hm >> (q + 1);   // run starts after q in this lane
+            const unsigned end = rest ? lane * VPE + q + 1u + (unsigned)(__ffs(rest) - 1) : after;
+            insert(e[q], end - (lane * VPE + q));
+          }
+        }
       }
     }
   }

@@ -32,6 +32,7 @@ def check(x, argsort=False):
     if argsort:
         _, perm = cafs.argsort(xt)
         assert np.array_equal(perm.cpu().numpy().view(np.uint32), O.stable_argsort(x))
+    return rep
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.int64])
@@ -66,3 +67,24 @@ def test_runs_in_every_table_form(k, mean_run, dtype):
     x = G.runs_column(700_001, k, mean_run, "uniform", dtype, seed=k + int(mean_run))
     check(x)
     check(x[::-1].copy())
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("n", [300_001, 1_048_573])
+@pytest.mark.parametrize("shape", ["grouped", "runs2", "runs40"])
+def test_run_folding_in_the_global_table(shape, n, dtype):
+    # K_hat above one CTA's shared table: the global-table counter folds runs
+    # of equal keys inside each warp's window of consecutive keys and inserts
+    # every run once with its length (Sec. 4.4).  Ragged lengths give scalar
+    # head and tail elements and chunks whose last warps hold fewer vectors;
+    # the type minimum (the table's empty marker) is one of the run values,
+    # and a window of all-distinct keys follows the plain per-key path.
+    k = 60_000
+    if shape == "grouped":
+        x = G.grouped_column(n, k, dtype, seed=n % 97)
+    else:
+        x = G.runs_column(n, k, 2.0 if shape == "runs2" else 40.0, "uniform", dtype, seed=n % 89)
+    x[x == x[n // 3]] = np.iinfo(dtype).min
+    x[-5000:] = G.column(5000, 5000, "uniform", dtype, seed=3)   # distinct tail
+    rep = check(x, argsort=(shape == "runs2" and n == 300_001))
+    assert rep["path"] in (O.MAIN, O.MAIN_OVERFLOW_RADIX, O.HIGH_ENTROPY_RADIX)
