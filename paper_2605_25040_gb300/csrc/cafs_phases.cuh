@@ -1247,8 +1247,12 @@ __device__ __forceinline__ unsigned radix_digit(K k, int shift) {
 //   + (rank within the tile).
 // (a) every CTA counts digit d over its range; (b) the CTAs scan those
 // counts (CTA b takes digits d = b, b + G, ...), with a grid barrier after
-// each step; (c) every CTA ranks each tile in shared memory (stable: a
-// per-warp match on the digit, warps in order) and writes it out.
+// each step; (c) every CTA ranks each tile in shared memory (stable: each
+// warp ranks its items by digit, item-major then lane, and the warps' digit
+// counts are scanned in warp order) and writes it out.  Per half-tile the
+// half meets at four barriers: after the warps' ranking, after the digit
+// scan (a thread pair per digit, the digit totals scanned within each warp),
+// after taking the digit bases, and after staging the keys in digit order.
 // Half-CTA pipelines of a radix pass: the CTA's range is cut into half-tiles
 // of kHalfTile keys, taken alternately by the two halves of the CTA (512
 // threads each, own shared memory, own named barrier).  A half-tile gets its
@@ -1308,41 +1312,14 @@ __device__ __forceinline__ void rank_warp_items(unsigned (&rd)[kRadixItems], uns
   }
 }
 
-// Exclusive scan of one value per thread of a half (all its threads call it).
-__device__ __forceinline__ unsigned half_exclusive_scan(unsigned v, unsigned* scratch, int h) {
-  const int t = threadIdx.x - h * kHalfThreads, w = t >> 5, l = t & 31;
-  unsigned x = v;
-  #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-    if (l >= o) x += y;
-  }
-  half_sync(h);
-  if (l == 31) scratch[w] = x;
-  half_sync(h);
-  if (w == 0) {
-    unsigned sw = (l < kHalfWarps) ? scratch[l] : 0u;
-    #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, sw, o);
-      if (l >= o) sw += y;
-    }
-    if (l < kHalfWarps) scratch[l] = sw;
-  }
-  half_sync(h);
-  return ((w > 0) ? scratch[w - 1] : 0u) + x - v;
-}
-
 template <typename K, bool PAY>
 struct HalfSmem {
   K stage_k[kHalfTile];
   unsigned stage_v[PAY ? kHalfTile : 1];
   unsigned short wcnt[kHalfWarps * kRadixDigits];
-  unsigned tile_cnt[kRadixDigits];
   unsigned tile_start[kRadixDigits];
   unsigned base[kRadixDigits];      // digit destination minus its first stage slot
-  unsigned scratch[kHalfWarps];
-  unsigned scan_part[kHalfThreads];
+  unsigned scratch[kHalfWarps];     // per warp: half-tile keys of its 16 digits
   unsigned stop;                    // the half leaves the pass (written before a barrier, read after it)
 };
 
@@ -1487,7 +1464,9 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
   for (unsigned long long q = (unsigned long long)h; q < nhalf; q += 2) {
     const unsigned long long base = i0 + q * kHalfTile;
     const unsigned cnt = (unsigned)((i1 - base) < (unsigned long long)kHalfTile ? (i1 - base) : kHalfTile);
-    half_sync(h);
+    // No barrier here: another warp's accesses of the previous half-tile's
+    // shared arrays all come before it reaches this half-tile's first
+    // barrier, and until then this warp writes only its own counter row.
     for (int d = lane; d < kRadixDigits; d += 32) hs->wcnt[w * kRadixDigits + d] = 0;
     __syncwarp();
     K key[kRadixItems];
@@ -1509,41 +1488,34 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     if (runs) rank_warp_items<true>(rd, hs->wcnt + w * kRadixDigits, lane);
     else rank_warp_items<false>(rd, hs->wcnt + w * kRadixDigits, lane);
     half_sync(h);
-    // Per digit: exclusive scan over the half's warps and the half-tile total.
-    {
-      constexpr int kScanGroups = kHalfThreads / kRadixDigits;
-      constexpr int kWarpsPerGroup = kHalfWarps / kScanGroups;
-      static_assert(kScanGroups * kRadixDigits == kHalfThreads, "scan groups");
-      const int d = t % kRadixDigits, g = t / kRadixDigits;
-      unsigned run = 0;
-      #pragma unroll
-      for (int qq = g * kWarpsPerGroup; qq < (g + 1) * kWarpsPerGroup; ++qq) {
-        const unsigned x = hs->wcnt[qq * kRadixDigits + d];
-        hs->wcnt[qq * kRadixDigits + d] = (unsigned short)run;
-        run += x;
-      }
-      hs->scan_part[g * kRadixDigits + d] = run;
-      half_sync(h);
-      unsigned before = 0, tot = 0;
-      #pragma unroll
-      for (int qq = 0; qq < kScanGroups; ++qq) {
-        const unsigned v = hs->scan_part[qq * kRadixDigits + d];
-        before += qq < g ? v : 0u;
-        tot += v;
-      }
-      if (g > 0) {
-        #pragma unroll
-        for (int qq = g * kWarpsPerGroup; qq < (g + 1) * kWarpsPerGroup; ++qq)
-          hs->wcnt[qq * kRadixDigits + d] = (unsigned short)(hs->wcnt[qq * kRadixDigits + d] + before);
-      }
-      if (g == 0) hs->tile_cnt[d] = tot;
+    // Digit d = t / 2: the thread pair (g = t & 1, adjacent lanes) turns the
+    // counts of warps 8g .. 8g + 7 into exclusive prefixes over the half's
+    // warps, and each warp scans the half-tile totals of its 16 digits, so
+    // that one barrier later every thread has its digit's start.
+    constexpr int kPairWarps = kHalfWarps / 2;
+    static_assert(kHalfThreads == 2 * kRadixDigits && kHalfWarps * 16 == kRadixDigits, "digit pairs");
+    const int dg = t >> 1, g = t & 1;
+    unsigned run = 0;
+    #pragma unroll
+    for (int qq = g * kPairWarps; qq < (g + 1) * kPairWarps; ++qq) {
+      const unsigned x = hs->wcnt[qq * kRadixDigits + dg];
+      hs->wcnt[qq * kRadixDigits + dg] = (unsigned short)run;
+      run += x;
     }
-    half_sync(h);
-    {
-      const unsigned v = t < kRadixDigits ? hs->tile_cnt[t] : 0u;
-      const unsigned ex = half_exclusive_scan(v, hs->scratch, h);
-      if (t < kRadixDigits) hs->tile_start[t] = ex;
+    const unsigned other = __shfl_xor_sync(0xffffffffu, run, 1);
+    const unsigned tot = run + other;   // the digit's keys in the half-tile
+    if (g) {
+      #pragma unroll
+      for (int qq = kPairWarps; qq < kHalfWarps; ++qq)
+        hs->wcnt[qq * kRadixDigits + dg] = (unsigned short)(hs->wcnt[qq * kRadixDigits + dg] + other);
     }
+    unsigned incl = g ? 0u : tot;        // inclusive scan over this warp's digits
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) hs->scratch[w] = incl;
     // Take this half-tile's digit bases from the cursor, in half-tile order.
     if (t == 0) {
       const unsigned long long t0 = global_timer_ns();
@@ -1563,9 +1535,16 @@ __device__ bool radix_pass(const Params& p, const K* in_k, const unsigned* in_v,
     }
     half_sync(h);
     if (hs->stop) break;
-    if (t < kRadixDigits) {
-      hs->base[t] = running[t] - hs->tile_start[t];   // destination of stage slot i = base[d] + i
-      running[t] += hs->tile_cnt[t];
+    {
+      unsigned wt = 0;   // half-tile keys of the digits of warps before this one
+      if (lane < w) wt = hs->scratch[lane];
+      const unsigned before = __reduce_add_sync(0xffffffffu, wt);
+      if (!g) {
+        const unsigned start = before + incl - tot;
+        hs->tile_start[dg] = start;
+        hs->base[dg] = running[dg] - start;   // destination of stage slot i = base[d] + i
+        running[dg] += tot;
+      }
     }
     half_sync(h);
     if (t == 0) {
