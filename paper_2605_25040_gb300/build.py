@@ -92,14 +92,40 @@ KERNEL_SOURCES = {
 }
 
 
+def strip_comments(src: bytes) -> bytes:
+    """C/C++ source without its // and /* */ comments (string and character
+    literals kept as they are), so that a comment edit does not count as a
+    change of the code."""
+    out = bytearray()
+    i, n = 0, len(src)
+    while i < n:
+        c = src[i:i + 1]
+        if c in (b'"', b"'"):
+            j = i + 1
+            while j < n and src[j:j + 1] != c:
+                j += 2 if src[j:j + 1] == b"\\" else 1
+            out += src[i:j + 1]
+            i = j + 1
+        elif src[i:i + 2] == b"//":
+            j = src.find(b"\n", i)
+            i = n if j < 0 else j
+        elif src[i:i + 2] == b"/*":
+            j = src.find(b"*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out += c
+            i += 1
+    return bytes(out)
+
+
 def kernel_source_hash(kernel: str, read=None) -> str:
-    """SHA-256 over the sources of one kernel family (KERNEL_SOURCES).
-    Profile summaries record it, so that a DRAM-traffic figure is reported
-    only for the code it was measured on.  ``read(relpath) -> bytes``
-    substitutes another tree (e.g. a git revision)."""
+    """SHA-256 over the sources of one kernel family (KERNEL_SOURCES), their
+    comments left out.  Profile summaries record it, so that a DRAM-traffic
+    figure is reported only for the code it was measured on.
+    ``read(relpath) -> bytes`` substitutes another tree (e.g. a git revision)."""
     import hashlib
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES[kernel]:
         data = read(rel) if read else open(os.path.join(ROOT, rel), "rb").read()
-        h.update(rel.encode() + b"\0" + data + b"\0")
+        h.update(rel.encode() + b"\0" + strip_comments(data) + b"\0")
     return h.hexdigest()

@@ -16,9 +16,9 @@
 //      table (main path, Sec. 4.2: a direct table of the sampled keys, linear
 //      probing over 16-byte buckets, or two-choice buckets) that is merged
 //      into a global table hashed with Eq. 4; above what a CTA's table holds,
-//      every key goes to the global table.  The global table counts distinct
-//      keys and raises the overflow guard when they exceed L = C/2 (Eq. 6,
-//      Alg. 4)
+//      every key goes to the global table, runs of equal keys folded first
+//      (Sec. 4.4).  The global table counts distinct keys; the branch is the
+//      overflow branch when they exceed L = C/2 (Eq. 6, Alg. 4)
 //   3  the K' (key, count) pairs are put in key order and their counts
 //      exclusive-scanned (Alg. 4): for K' <= 4096 every CTA computes, for its
 //      share of the pairs, the rank and the run offset directly (number of
