@@ -534,6 +534,12 @@ __device__ __forceinline__ int table_log2(unsigned long long C, unsigned long lo
   return log2_pow2(big < cap ? big : (cap > C ? cap : C));
 }
 
+// Counter increment without a returned value: a reduction that L2 applies
+// on its own, no response back to the SM.
+__device__ __forceinline__ void red_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long long key64, unsigned inc) {
   Ctrl* c = g.ctrl;
   const int lg = table_log2(g.C, g.cap, g.logC);
@@ -551,7 +557,7 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
     const unsigned long long slot = (h + probe) & mask;
     const unsigned long long k = ld_relaxed_u64(g.keys + slot);
     if (k == key64) {
-      atomicAdd(g.counts + slot, inc);
+      red_add_u32(g.counts + slot, inc);
       return;
     }
     if (k == kEmpty64) {
@@ -566,7 +572,7 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
         if ((int)(threadIdx.x & 31u) == lead) first = atomicAdd(&c->occupancy, (unsigned)__popc(grp));
         const unsigned idx = __shfl_sync(grp, first, lead) + (unsigned)__popc(grp & lanemask_lt());
         if (idx < size) g.claimed[idx] = (unsigned)slot;
-        atomicAdd(g.counts + slot, inc);
+        red_add_u32(g.counts + slot, inc);
         if (idx >= limit) {
           if (!ld_relaxed_u32(&c->overflow)) atomicExch(&c->overflow, 1u);
           if (g.stop) *reinterpret_cast<volatile unsigned*>(g.stop) = 1u;
@@ -574,7 +580,7 @@ static __device__ __noinline__ void global_insert(GlobalTable g, unsigned long l
         return;
       }
       if (old == key64) {
-        atomicAdd(g.counts + slot, inc);
+        red_add_u32(g.counts + slot, inc);
         return;
       }
     }
